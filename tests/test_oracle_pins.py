@@ -1,0 +1,399 @@
+"""Pins of the C oracle against facts that do not come from the oracle itself:
+values the paper prints, hand evaluations of Eq. 6, closed forms of the GI
+Hamiltonian (Eq. 8), brute force over all spin states and all vertex
+permutations, an independent Philox implementation, and invariants of Eq. 6.
+"""
+import itertools
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# ---------------------------------------------------------------- Eq. 10, Table 4
+def test_tts_table4_worked_examples():
+    for method, N, ps, t, tts in _rows("table4_tts.txt"):
+        got = O.tts(float(t), float(ps), 0.99)
+        if tts == "inf":
+            assert math.isinf(got) and got > 0, (method, N)
+        elif float(tts) == 0.0:
+            assert got == 0.0, (method, N)
+        else:
+            assert abs(got / float(tts) - 1) < 0.01, (method, N, got, tts)
+
+
+# ------------------------------------------------------- Table 2/3, Eq. 9 examples
+def test_iterations_table3():
+    for case, EC, tau, R, it in _rows("table3_iterations.txt"):
+        assert O.iterations(float(EC), float(R), float(tau), 3.0) == float(it), case
+    # SC = EC / R examples after Eq. 9
+    assert 20000 / 10 == 2000 and 20000 / 40 == 500
+    # 400 cycles per iteration for beta = 3, tau = 100 (Sec. 4.2)
+    assert O.iterations(400.0, 1.0, 100.0, 3.0) == 1.0
+
+
+def test_jperp_schedule_table2():
+    # J_perp 0 -> 0.5 in beta = 3 steps every tau = 100 cycles, reset at each
+    # 400-cycle iteration; scaled by S = 12: 0, 2, 4, 6.
+    seq = [O.jperp(t, 0, 6, 3, 100) for t in range(0, 1200)]
+    for it in range(3):
+        base = 400 * it
+        assert seq[base:base + 100] == [0] * 100
+        assert seq[base + 100:base + 200] == [2] * 100
+        assert seq[base + 200:base + 300] == [4] * 100
+        assert seq[base + 300:base + 400] == [6] * 100
+
+
+def test_ssa_i0_schedule_sec44():
+    # I0 from 1 to 16, multiplied by 1/beta = 2 every tau = 10 cycles:
+    # 5 levels, 50 cycles per iteration (Sec. 4.4); scaled by S = 12.
+    want = []
+    for lv in (12, 24, 48, 96, 192):
+        want += [lv] * 10
+    got = [O.ssa_i0(t, 12, 192, 2, 10) for t in range(100)]
+    assert got == want + want
+
+
+# ------------------------------------------------------------------- SplitMix64
+def test_splitmix64_published_first_output():
+    # first output of SplitMix64 from state 0 (Steele et al. 2014 reference)
+    assert int(O.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
+
+
+# ----------------------------------------------------------------------- Philox
+_TRITON_SNIPPET = r"""
+import os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+@triton.jit
+def k(out_ptr, seed, c0, c1, c2, c3):
+    z = tl.zeros([1], tl.int32)
+    a, b, c, d = tl.philox(seed, (c0 + z).to(tl.uint32, bitcast=True), (c1 + z).to(tl.uint32, bitcast=True), (c2 + z).to(tl.uint32, bitcast=True), (c3 + z).to(tl.uint32, bitcast=True), 10)
+    o = tl.arange(0, 1)
+    tl.store(out_ptr + o, a); tl.store(out_ptr + 1 + o, b)
+    tl.store(out_ptr + 2 + o, c); tl.store(out_ptr + 3 + o, d)
+for line in sys.stdin:
+    seed, c0, c1, c2, c3 = (int(x) for x in line.split())
+    seed = seed - (1 << 64) if seed >= (1 << 63) else seed
+    cs = [c - (1 << 32) if c >= (1 << 31) else c for c in (c0, c1, c2, c3)]
+    o = torch.zeros(4, dtype=torch.int32)
+    k[(1,)](o, seed, *cs)
+    print(" ".join(str(int(x) & 0xffffffff) for x in o))
+"""
+
+
+def test_philox_matches_independent_library():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    cases = [(0, 0, 0, 0, 0), ((1 << 64) - 1, 2**32 - 1, 2**32 - 1, 2**32 - 1, 2**32 - 1)]
+    for _ in range(6):
+        cases.append((int(rng.integers(0, 2**63)) * 2 + 1,) + tuple(int(x) for x in rng.integers(0, 2**32, 4)))
+    inp = "\n".join(" ".join(str(v) for v in c) for c in cases) + "\n"
+    try:
+        res = subprocess.run([sys.executable, "-c", _TRITON_SNIPPET], input=inp, capture_output=True,
+                             text=True, timeout=600)
+    except subprocess.TimeoutExpired:
+        pytest.skip("triton interpreter too slow here")
+    if res.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + res.stderr.strip().splitlines()[-1][:200])
+    lines = res.stdout.strip().splitlines()
+    assert len(lines) == len(cases)
+    for c, ln in zip(cases, lines):
+        seed = c[0]
+        want = [int(x) for x in ln.split()]
+        got = O.philox4x32_10(list(c[1:]), [seed & 0xFFFFFFFF, seed >> 32])
+        assert [int(x) for x in got] == want, c
+
+
+def test_noise_bits_balanced_and_distinct():
+    # the per-spin bits are fair and differ across replica, trial and cycle
+    bits = np.array([[O.noise_bit(5, i, k, 3, 17) for i in range(256)] for k in range(8)])
+    assert 0.4 < bits.mean() < 0.6
+    assert not np.array_equal(bits[0], bits[1])
+    b2 = np.array([O.noise_bit(5, i, 0, 4, 17) for i in range(256)])
+    b3 = np.array([O.noise_bit(5, i, 0, 3, 18) for i in range(256)])
+    assert not np.array_equal(bits[0], b2) and not np.array_equal(bits[0], b3)
+
+
+def test_noise_bit_layout_definition():
+    # spin i: Philox(ctr=(i/128, k, trial, t)), word (i%128)/32, bit 15-e/2 (even e)
+    # or 31-(e-1)/2 (odd e), e = i % 32
+    seed, k, trial, t = 0x1234_5678_9ABC_DEF1, 2, 9, 44
+    for i in (0, 1, 2, 31, 32, 77, 127, 128, 300):
+        w = O.philox4x32_10([i // 128, k, trial, t], [seed & 0xFFFFFFFF, seed >> 32])[(i % 128) // 32]
+        e = i % 32
+        b = 31 - (e >> 1) if e & 1 else 15 - (e >> 1)
+        assert O.noise_bit(seed, i, k, trial, t) == (int(w) >> b) & 1
+
+
+# ----------------------------------------------------------- graphs, Eq. 8, Ising
+def _isomorphisms(adj1, adj2):
+    """All phi: V2 -> V1 with adj2[u][v] == adj1[phi(u)][phi(v)] (brute force)."""
+    n = adj1.shape[0]
+    out = []
+    for phi in itertools.permutations(range(n)):
+        if all(adj2[u, v] == adj1[phi[u], phi[v]] for u in range(n) for v in range(n)):
+            out.append(phi)
+    return out
+
+
+def test_er_graph_and_permutation_properties():
+    a = O.gen_er_graph(40, 1 << 31, 11)
+    assert (a == a.T).all() and (np.diag(a) == 0).all()
+    dens = a.sum() / (40 * 39)
+    assert 0.4 < dens < 0.6
+    b, perm = O.permute_graph(a, 12)
+    assert sorted(perm.tolist()) == list(range(40))
+    assert all(b[perm[u], perm[v]] == a[u, v] for u in range(40) for v in range(40))
+    # Fisher-Yates positions are uniform over many seeds
+    counts = np.zeros((5, 5))
+    for s in range(2000):
+        _, p = O.permute_graph(np.zeros((5, 5), np.uint8), s)
+        counts[np.arange(5), p] += 1
+    assert counts.min() > 400 * 0.8 and counts.max() < 400 * 1.2
+    # p = 0.3 / 0.7 densities
+    for p in (0.3, 0.7):
+        g = O.gen_er_graph(60, int(p * 2**32), 5)
+        assert abs(g.sum() / (60 * 59) - p) < 0.05
+
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (4, 2), (5, 3)])
+def test_qubo_expansion_equals_eq8(n, seed):
+    a = O.gen_er_graph(n, 1 << 31, seed)
+    b, _ = O.permute_graph(a, seed + 100)
+    b[0, 1] ^= 1  # also non-isomorphic-ish pairs
+    b[1, 0] ^= 1
+    rng = np.random.default_rng(seed)
+    for C1, C2 in ((1, 1), (3, 2)):
+        Q, c = O.gi_qubo(a, b, C1, C2)
+        assert (np.tril(Q, -1) == 0).all()
+        for _ in range(200):
+            x = rng.integers(0, 2, n * n).astype(np.uint8)
+            assert O.qubo_value(Q, c, x) == O.gi_hamiltonian(a, b, C1, C2, x)
+
+
+@pytest.mark.parametrize("n,seed", [(3, 4), (3, 5)])
+def test_ising_conversion_exhaustive(n, seed):
+    # S * H_QUBO(x) == E'(sigma) + offset' for every x (Sec. 4.2, sigma = 2x - 1)
+    a = O.gen_er_graph(n, 1 << 31, seed)
+    b, _ = O.permute_graph(a, seed)
+    for C1, C2, S in ((1, 1, 12), (2, 3, 4)):
+        Q, c = O.gi_qubo(a, b, C1, C2)
+        h, J, off = O.qubo_to_ising(Q, c, S)
+        assert (J == J.T).all() and (np.diag(J) == 0).all()
+        xs = np.array(list(itertools.product([0, 1], repeat=n * n)), dtype=np.uint8)
+        E = O.ising_energy(h, J, (2 * xs.astype(np.int8) - 1))
+        for x, e in zip(xs, E):
+            assert S * O.gi_hamiltonian(a, b, C1, C2, x) == e + off
+
+
+@pytest.mark.parametrize("n,seed,iso", [(3, 1, True), (4, 6, True), (4, 8, True), (4, 9, False), (3, 2, False)])
+def test_ground_states_are_isomorphisms_bruteforce(n, seed, iso):
+    a = O.gen_er_graph(n, 1 << 31, seed)
+    b, perm = O.permute_graph(a, seed + 7)
+    if not iso:
+        b = b.copy()
+        b[0, n - 1] ^= 1
+        b[n - 1, 0] ^= 1
+    h, J, off = O.build_gi_ising(a, b)
+    N = n * n
+    xs = np.array(list(itertools.product([0, 1], repeat=N)), dtype=np.uint8)
+    E = O.ising_energy(h, J, 2 * xs.astype(np.int8) - 1)
+    isos = _isomorphisms(a, b)
+    assert bool(isos) == iso
+    if iso:
+        assert E.min() == -off  # Eq. 8 is zero exactly on isomorphisms
+        argmin = {tuple(x) for x in xs[E == E.min()]}
+        want = set()
+        for phi in isos:
+            x = np.zeros(N, np.uint8)
+            for u in range(n):
+                x[u * n + phi[u]] = 1
+            want.add(tuple(x))
+        assert argmin == want
+    else:
+        assert E.min() > -off
+
+
+def test_planted_permutation_has_ground_energy_and_closed_form_h_J():
+    n = 7
+    a = O.gen_er_graph(n, 1 << 31, 21)
+    b, perm = O.permute_graph(a, 22)
+    h, J, off = O.build_gi_ising(a, b)
+    N = n * n
+    inv = np.argsort(perm)
+    x = np.zeros(N, np.int8)
+    for u in range(n):
+        x[u * n + inv[u]] = 1
+    assert O.ising_energy(h, J, 2 * x - 1) == -off
+    # closed forms for C1 = C2 = 1, S = 12: J' in {0, -6}; h'_a = 12(2 - n) - 6 m_a
+    for u in range(n):
+        for i in range(n):
+            m = sum(1 for v in range(n) for j in range(n)
+                    if v != u and j != i and a[i, j] != b[u, v])
+            assert h[u * n + i] == 12 * (2 - n) - 6 * m
+            for v in range(n):
+                for j in range(n):
+                    if (u, i) == (v, j):
+                        continue
+                    linked = (u == v) or (i == j) or (a[i, j] != b[u, v])
+                    assert J[u * n + i, v * n + j] == (-6 if linked else 0)
+
+
+# ------------------------------------------------------------------ Eq. 6, by hand
+def test_hand_trace_field_and_clamps():
+    h = np.array([3, -2])
+    J = np.array([[0, -6], [-6, 0]])
+    state = dict(sigma=np.array([[[1, -1], [-1, -1], [-1, 1]]], np.int8),
+                 hist=np.array([[[[-1, 1], [1, -1], [1, 1]]]], np.int8),
+                 Is=np.array([[[5, -3], [0, 9], [-9, 2]]], np.int32))
+    rows = _rows("hand_trace_field_clamp.txt")
+    for T in (1, 2, 3):
+        out = O.anneal(h, J, R=3, cycles=T, trials=1, seed=0, I0=10, alpha=1, n_rnd=0,
+                       jperp_min=2, jperp_max=6, beta=2, tau=1, delay=1, init_mode=2, state=state)
+        for t, k, s0, s1, i0, i1 in rows:
+            if int(t) == T:
+                k = int(k)
+                assert out["sigma"][0, k].tolist() == [int(s0), int(s1)], (T, k)
+                assert out["Is"][0, k].tolist() == [int(i0), int(i1)], (T, k)
+
+
+@pytest.mark.parametrize("mode", ["upper", "both"])
+def test_hand_trace_delay_and_ring(mode):
+    h = np.array([0])
+    J = np.array([[0]])
+    state = dict(sigma=np.array([[[1], [-1], [1]]], np.int8),
+                 hist=np.array([[[[-1], [-1], [1]], [[1], [1], [-1]]]], np.int8),
+                 Is=np.array([[[1], [-2], [0]]], np.int32))
+    for m, t, s0, s1, s2, i0, i1, i2 in _rows("hand_trace_delay_ring.txt"):
+        if m != mode:
+            continue
+        out = O.anneal(h, J, R=3, cycles=int(t), trials=1, seed=0, I0=100, alpha=1, n_rnd=0,
+                       jperp_min=3, jperp_max=3, beta=1, tau=1, delay=2, init_mode=2,
+                       coupling_both=int(mode == "both"), state=state)
+        assert out["sigma"][0, :, 0].tolist() == [int(s0), int(s1), int(s2)], t
+        assert out["Is"][0, :, 0].tolist() == [int(i0), int(i1), int(i2)], t
+
+
+def test_constant_bias_clamp_sequence():
+    # J = 0, no noise, no coupling, h = c: Is(t) = clamp of t*c by Eq. 6b
+    h = np.array([5, -7, 0])
+    J = np.zeros((3, 3), np.int64)
+    want = {1: [5, -7, 0], 2: [10, -14, 0], 3: [15, -21, 0], 4: [20, -24, 0], 5: [23, -24, 0], 6: [23, -24, 0]}
+    for T, w in want.items():
+        out = O.anneal(h, J, R=1, cycles=T, trials=1, seed=1, n_rnd=0, jperp_max=0, init_mode=1)
+        assert out["Is"][0, 0].tolist() == w
+        assert out["sigma"][0, 0].tolist() == [1, -1, 1]
+
+
+def test_pure_noise_random_walk_uses_philox_bits():
+    # h = J = J_perp = 0: Is is a +-n_rnd walk clamped to [-I0, I0 - alpha],
+    # driven by the Philox bits (pinned above against an independent library)
+    N, R, T, seed = 40, 2, 30, 99
+    out = O.anneal(np.zeros(N), np.zeros((N, N)), R=R, cycles=T, trials=1, seed=seed,
+                   trial_offset=5, jperp_max=0, I0=24, alpha=1, n_rnd=12)
+    for k in range(R):
+        for i in range(N):
+            s = 0
+            for t in range(T):
+                r = -1 if O.noise_bit(seed, i, k, 5, t) else 1
+                v = s + 12 * r
+                s = 23 if v >= 24 else (-24 if v < -24 else v)
+            assert out["Is"][0, k, i] == s
+            assert out["sigma"][0, k, i] == (1 if s >= 0 else -1)
+
+
+def test_initial_state_from_philox():
+    N, R, seed = 30, 3, 77
+    out = O.anneal(np.zeros(N), np.zeros((N, N)), R=R, cycles=0, trials=1, seed=seed, trial_offset=2)
+    for k in range(R):
+        for i in range(N):
+            assert out["sigma"][0, k, i] == (-1 if O.noise_bit(seed, i, k, 2, 0xFFFFFFFF) else 1)
+
+
+# -------------------------------------------------------------------- invariants
+def _gi(n=5, seed=3):
+    a = O.gen_er_graph(n, 1 << 31, seed)
+    b, _ = O.permute_graph(a, seed + 1)
+    return O.build_gi_ising(a, b)
+
+
+def test_counter_bounds_and_sign_invariant():
+    h, J, off = _gi()
+    for T in (1, 7, 60):
+        out = O.anneal(h, J, R=4, cycles=T, trials=3, seed=T, tau=5)
+        assert out["Is"].min() >= -24 and out["Is"].max() <= 23
+        assert ((out["Is"] >= 0) == (out["sigma"] == 1)).all()
+
+
+def test_replicas_independent_of_R_without_coupling():
+    h, J, off = _gi()
+    a = O.anneal(h, J, R=2, cycles=40, trials=2, seed=5, jperp_max=0)
+    b = O.anneal(h, J, R=5, cycles=40, trials=2, seed=5, jperp_max=0)
+    assert np.array_equal(a["sigma"], b["sigma"][:, :2])
+    assert np.array_equal(a["Is"], b["Is"][:, :2])
+
+
+def test_trials_independent_of_batch():
+    h, J, off = _gi()
+    full = O.anneal(h, J, R=3, cycles=50, trials=4, seed=9, tau=10)
+    one = O.anneal(h, J, R=3, cycles=50, trials=1, seed=9, tau=10, trial_offset=2)
+    assert np.array_equal(full["sigma"][2], one["sigma"][0])
+    assert np.array_equal(full["E_final"][2], one["E_final"][0])
+
+
+def test_checkpoint_resume_equals_straight_run():
+    h, J, off = _gi()
+    for d in (0, 1, 2):
+        straight = O.anneal(h, J, R=3, cycles=70, trials=2, seed=4, tau=7, delay=d)
+        first = O.anneal(h, J, R=3, cycles=30, trials=2, seed=4, tau=7, delay=d)
+        resumed = O.anneal(h, J, R=3, cycles=40, trials=2, seed=4, tau=7, delay=d,
+                           init_mode=2, start_cycle=30, state=first)
+        for key in ("sigma", "Is", "E_final", "hist"):
+            assert np.array_equal(straight[key], resumed[key]), (d, key)
+
+
+def test_energy_tracking_consistent():
+    h, J, off = _gi()
+    out = O.anneal(h, J, R=4, cycles=120, trials=2, seed=8, tau=10, track_best=True)
+    assert (out["E_best"] <= out["E_final"]).all()
+    assert (out["E_best"] >= -off).all()
+    assert ((out["best_cycle"] >= 1) & (out["best_cycle"] <= 120)).all()
+    np.testing.assert_array_equal(out["E_final"], O.ising_energy(h, J, out["sigma"]))
+    # E_best is the energy of sigma at best_cycle
+    for tr in range(2):
+        for k in range(4):
+            c = int(out["best_cycle"][tr, k])
+            part = O.anneal(h, J, R=4, cycles=c, trials=1, seed=8, tau=10, trial_offset=tr)
+            assert part["E_final"][0, k] == out["E_best"][tr, k]
+
+
+def test_r1_without_coupling_is_ssa_eq2():
+    # SSQA with R = 1, J_perp = 0 and a fixed I0 reduces to SSA (Eq. 2)
+    h, J, off = _gi()
+    q = O.anneal(h, J, R=1, cycles=90, trials=1, seed=12, trial_offset=3, jperp_max=0,
+                 I0=24, alpha=1, n_rnd=12)
+    s, Is = O.ssa(h, J, cycles=90, seed=12, trial=3, i0_min=24, i0_max=24, i0_mult=2, tau=10, n_rnd=12)
+    assert np.array_equal(q["sigma"][0, 0], s)
+    assert np.array_equal(q["Is"][0, 0], Is)
+
+
+def test_ssqa_finds_planted_ground_state_small():
+    # with the paper's constants (Table 2) a 4-vertex GI instance is solved
+    a = O.gen_er_graph(4, 1 << 31, 31)
+    b, _ = O.permute_graph(a, 32)
+    h, J, off = O.build_gi_ising(a, b)
+    out = O.anneal(h, J, R=8, cycles=400, trials=8, seed=33)
+    assert (out["E_final"].min(axis=1) == -off).mean() >= 0.5
