@@ -1,0 +1,323 @@
+"""Benchmark: SSQA spin-updates/s on the batched GI workload (N = 400 spins,
+R = 16 replicas, 2000 cycles, 1024 trials per GPU), one JSON line on stdout.
+
+A step is one full anneal of the whole batch (every cycle of Eq. 6 for all
+spins x replicas x trials) through ssqa_anneal with device-resident buffers.
+`e2e` repeats the step through the same C ABI with host buffers (instance
+upload, anneal, result download inside the timed region).  `--impl
+reference` times the C oracle on the host cores on a bounded sample of the
+same workload.  Multi-GPU runs shard trials across ranks (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batched_gi_n20"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------ oracle (CPU)
+def _oracle_trial(args):
+    h, J, kw, tr = args
+    from oracle import oracle as O
+
+    t0 = time.perf_counter()
+    O.anneal(h, J, trial_offset=tr, **kw)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(h, J, cfg, cycles, ntrials, cores):
+    """Spin-updates/s of the oracle: `ntrials` single-trial anneals of
+    `cycles` cycles, spread over `cores` spawned worker processes."""
+    kw = dict(R=cfg["R"], cycles=cycles, trials=1, seed=cfg["seed"], tau=cfg["tau"])
+    jobs = [(h, J, kw, tr) for tr in range(ntrials)]
+    t0 = time.perf_counter()
+    if cores > 1:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_trial, jobs)
+    else:
+        for j in jobs:
+            _oracle_trial(j)
+    wall = time.perf_counter() - t0
+    return h.shape[0] * cfg["R"] * cycles * ntrials / wall, wall
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, dev=0):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9 or f[0] != str(dev):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2302_12454_gb300 as S
+    from paper_2302_12454_gb300 import build as B
+    from paper_2302_12454_gb300 import workloads as W
+
+    B.build()
+    cfg = dict(W.CONFIGS[WORKLOAD])
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    n, R, cycles, trials = cfg["n"], cfg["R"], cfg["cycles"], cfg["trials"]
+    a = S.gen_er_graph(n, W.p_q32(cfg["p"]), cfg["graph_seed"])
+    b, _ = S.permute_graph(a, cfg["perm_seed"])
+    I = S.Ising.gi(a, b)
+    h, J, off = I.export()
+    N = n * n
+    cols = trials * R
+    offset = rank * trials  # weak scaling: each rank anneals its own trial range
+    params = S.make_params(R=R, cycles=cycles, trials=trials, seed=cfg["seed"], tau=cfg["tau"],
+                           trial_offset=offset, algo=S.ALGO_TENSOR)
+    dev = torch.device("cuda")
+    sigma = torch.empty((trials, R, N), dtype=torch.int8, device=dev)
+    Is = torch.empty((trials, R, N), dtype=torch.int32, device=dev)
+    E = torch.empty((trials, R), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        S.anneal_device(I, params, sigma, Is, e_final=E, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{rank}.csv")
+                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/ssqa_clocks_{rank}.csv")
+    wall0 = time.perf_counter()
+    with clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t_total = sum(ms) / 1e3
+    if dist:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    updates_per_step = N * R * cycles * trials
+    value = updates_per_step * args.steps * world / t_total
+    ms_per_step = t_total / args.steps * 1e3
+
+    # results of the last step: success probability and time to solution
+    e_min = E.min(dim=1).values.cpu().numpy()
+    p_s = float((e_min == -off).mean())
+    t_trial = t_total / args.steps / trials
+    tts = S.tts(t_trial, p_s, 0.99)
+
+    # end to end through the C ABI with host buffers: instance upload,
+    # anneal, result download inside the timed region (pinned host memory)
+    hJ = torch.from_numpy(J).pin_memory().numpy()
+    hh = torch.from_numpy(h).pin_memory().numpy()
+    e2e_t = []
+    for k in range(max(1, min(args.steps, 3)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ik = S.Ising.dense(hJ, hh, off)
+        outk = S.anneal(Ik, R=R, cycles=cycles, trials=trials, seed=cfg["seed"], tau=cfg["tau"],
+                        trial_offset=offset, algo=S.ALGO_TENSOR)
+        e2e_t.append(time.perf_counter() - t0)
+        del Ik
+    e2e_t = e2e_t[1:]  # first call includes one-time context and allocator set-up
+    e2e_val = updates_per_step * world / float(np.mean(e2e_t))
+    h2d = J.nbytes + h.nbytes  # the step's inputs: couplings and biases (device images derive from them)
+    d2h = outk["sigma"].nbytes + outk["Is"].nbytes + outk["E_final"].nbytes
+    assert np.array_equal(outk["E_final"].min(axis=1) == -off, e_min == -off)
+
+    # plain GPU path (one launch per cycle) on the same workload, 1 step
+    Ip = S.Ising.gi(a, b)
+    pp = S.make_params(R=R, cycles=cycles, trials=trials, seed=cfg["seed"], tau=cfg["tau"], trial_offset=offset,
+                       algo=S.ALGO_PLAIN)
+    S.anneal_device(Ip, pp, sigma, Is, e_final=E, stream=stream)  # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.anneal_device(Ip, pp, sigma, Is, e_final=E, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    plain_val = updates_per_step / plain_s
+
+    peaks, src = _peaks()
+    fp8_peak = 2.0 * peaks["bf16_tflops"]  # FP8 dense = 2x BF16 (nominal 4.5 / 2.25 PF)
+    flop = 2.0 * N * updates_per_step  # 2N FLOP (N MACs) per spin update
+    achieved = flop / (t_total / args.steps) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("ssqa_tc_kernel_batched_gi_n20")
+        except Exception:
+            traffic = None
+    out = {
+        "metric": "spin-updates/sec",
+        "value": value,
+        "unit": "spin-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "fp8",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: GI n={n} (N={N} spins), ER p=0.5, planted permutation; R={R}, "
+                               f"{cycles} cycles, {trials} trials per GPU, one persistent launch",
+                   "N": N, "R": R, "cycles": cycles, "trials_per_gpu": trials,
+                   "l2": "flushed between timed steps (256 MiB write outside the timed events)"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp8_peak, "traffic": traffic,
+                     "peak_source": f"{src}: 2 x bf16_tflops (FP8 dense / BF16 dense = 2)"},
+        "e2e": {"value": e2e_val, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "tts_s": tts, "p_s": p_s, "t_per_trial_s": t_trial,
+        "plain_gpu": {"value": plain_val, "unit": "spin-updates/s", "ratio": value / world / plain_val,
+                      "note": "one kernel launch per cycle, CUDA cores (dp4a), same workload, 1 GPU"},
+        "wall_s": wall,
+    }
+    if rank == 0:
+        out["clocks"] = clk.summary(int(os.environ.get("LOCAL_RANK", 0)))
+        if not args.no_cpu_baseline:
+            cores = min(16, os.cpu_count() or 1)
+            rate, cwall = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, 300, cores, cores)
+            out["cpu_baseline"] = {"value": rate, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                                   "sample": f"{cores} trials x 300 cycles of the same workload, one "
+                                             f"single-threaded oracle process per core ({cwall:.1f} s)"}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2302_12454_gb300 import workloads as W
+    from oracle import oracle as O
+
+    O.build()
+    cfg = dict(W.CONFIGS[WORKLOAD])
+    a = O.gen_er_graph(cfg["n"], W.p_q32(cfg["p"]), cfg["graph_seed"])
+    b, _ = O.permute_graph(a, cfg["perm_seed"])
+    h, J, off = O.build_gi_ising(a, b)
+    cores = min(16, os.cpu_count() or 1)
+    cycles = 100
+    for _ in range(args.warmup):
+        oracle_rate(h, J, cfg, 20, cores, cores)
+    rates, walls = [], []
+    for _ in range(args.steps):
+        r, w = oracle_rate(h, J, cfg, cycles, cores, cores)
+        rates.append(r)
+        walls.append(w)
+    value = float(cycles * cores * h.shape[0] * cfg["R"] * len(walls) / sum(walls))
+    sample = f"{cores} trials x {cycles} cycles per step (one single-threaded oracle process per core)"
+    out = {"impl": "reference", "metric": "spin-updates/sec", "value": value, "unit": "spin-updates/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sum(walls) / len(walls) * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": f"{WORKLOAD} (bounded sample: {sample})"},
+           "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+"""Python binding of the SSQA C-ABI library (include/ssqa.h).
+
+Argument marshalling only: every step of an anneal runs in the CUDA kernels
+of ``libssqa.so``.  The library must have been built (``build.build()``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libssqa.so")
+
+OK, PENDING = 0, 1
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, ERR_DEVICE, ERR_NOT_FOUND = -1, -2, -3, -4, -5, -6, -7
+COUPLING_UPPER, COUPLING_BOTH = 0, 1
+INIT_RANDOM, INIT_ALL_MINUS, INIT_FROM_STATE = 0, 1, 2
+ALGO_AUTO, ALGO_PLAIN, ALGO_TENSOR = 0, 1, 2
+FLAG_TRACK_BEST, FLAG_DEVICE_PTRS = 1, 2
+
+
+class SSQAError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ssqa error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("R", ctypes.c_int32), ("cycles", ctypes.c_int32), ("trials", ctypes.c_int32),
+        ("I0", ctypes.c_int32), ("alpha", ctypes.c_int32), ("n_rnd", ctypes.c_int32),
+        ("jperp_min", ctypes.c_int32), ("jperp_max", ctypes.c_int32), ("beta", ctypes.c_int32),
+        ("tau", ctypes.c_int32), ("delay", ctypes.c_int32), ("coupling", ctypes.c_int32),
+        ("init_mode", ctypes.c_int32), ("algo", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("start_cycle", ctypes.c_int32), ("trial_offset", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("sigma", ctypes.c_void_p), ("sigma_hist", ctypes.c_void_p), ("is_state", ctypes.c_void_p),
+        ("e_final", ctypes.c_void_p), ("e_best", ctypes.c_void_p), ("best_cycle", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libssqa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2302_12454_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64
+        L.ssqa_gen_er_graph.argtypes = [i32, u32, u64, vp]
+        L.ssqa_permute_graph.argtypes = [i32, vp, u64, vp, vp]
+        L.ssqa_build_gi_ising.argtypes = [i32, vp, vp, i32, i32, i32, ctypes.POINTER(vp)]
+        L.ssqa_ising_from_dense.argtypes = [i32, vp, vp, i64, ctypes.POINTER(vp)]
+        L.ssqa_ising_free.argtypes = [vp]
+        L.ssqa_ising_free.restype = None
+        L.ssqa_ising_export.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), vp, vp]
+        L.ssqa_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.ssqa_params_default.restype = None
+        L.ssqa_anneal.argtypes = [vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
+        L.ssqa_energy.argtypes = [vp, vp, i64, vp, u32, vp]
+        L.ssqa_tts.argtypes = [ctypes.c_double] * 3
+        L.ssqa_tts.restype = ctypes.c_double
+        L.ssqa_last_error.argtypes = []
+        L.ssqa_last_error.restype = ctypes.c_char_p
+        L.ssqa_server_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
+        L.ssqa_server_destroy.argtypes = [vp]
+        L.ssqa_server_destroy.restype = None
+        L.ssqa_submit.argtypes = [vp, vp, ctypes.POINTER(Params), ctypes.POINTER(u64)]
+        L.ssqa_poll.argtypes = [vp, u64, ctypes.POINTER(Result), i32, ctypes.POINTER(ctypes.c_double)]
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().ssqa_last_error().decode()
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        raise SSQAError(rc, f"{what}: {last_error()}")
+    return rc
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())  # torch tensor
+
+
+# ---------------------------------------------------------------- instances
+def gen_er_graph(n: int, p_q32: int, seed: int) -> np.ndarray:
+    adj = np.zeros((n, n), np.uint8)
+    _check(lib().ssqa_gen_er_graph(n, p_q32, seed, _ptr(adj)), "gen_er_graph")
+    return adj
+
+
+def permute_graph(adj: np.ndarray, seed: int):
+    adj = np.ascontiguousarray(adj, np.uint8)
+    out = np.zeros_like(adj)
+    perm = np.zeros(adj.shape[0], np.int32)
+    _check(lib().ssqa_permute_graph(adj.shape[0], _ptr(adj), seed, _ptr(out), _ptr(perm)), "permute_graph")
+    return out, perm
+
+
+class Ising:
+    """Library-owned Ising instance (freed with the Python object)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @classmethod
+    def gi(cls, adj1, adj2, C1: int = 1, C2: int = 1, scale: int = 12) -> "Ising":
+        a1 = np.ascontiguousarray(adj1, np.uint8)
+        a2 = np.ascontiguousarray(adj2, np.uint8)
+        out = ctypes.c_void_p()
+        _check(lib().ssqa_build_gi_ising(a1.shape[0], _ptr(a1), _ptr(a2), C1, C2, scale, ctypes.byref(out)),
+               "build_gi_ising")
+        return cls(out.value)
+
+    @classmethod
+    def dense(cls, J, h, e_offset: int = 0) -> "Ising":
+        J = np.ascontiguousarray(J, np.int8)
+        h = np.ascontiguousarray(h, np.int32)
+        out = ctypes.c_void_p()
+        _check(lib().ssqa_ising_from_dense(h.shape[0], _ptr(J), _ptr(h), e_offset, ctypes.byref(out)),
+               "ising_from_dense")
+        return cls(out.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self):
+        N = ctypes.c_int32()
+        off = ctypes.c_int64()
+        _check(lib().ssqa_ising_export(self._h, ctypes.byref(N), ctypes.byref(off), None, None), "export")
+        h = np.zeros(N.value, np.int32)
+        J = np.zeros((N.value, N.value), np.int8)
+        _check(lib().ssqa_ising_export(self._h, None, None, _ptr(h), _ptr(J)), "export")
+        return h, J, off.value
+
+    @property
+    def N(self) -> int:
+        N = ctypes.c_int32()
+        _check(lib().ssqa_ising_export(self._h, ctypes.byref(N), None, None, None), "export")
+        return N.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and self._h.value and _lib is not None:
+            _lib.ssqa_ising_free(self._h)
+            self._h = None
+
+
+# ------------------------------------------------------------------ anneal
+PAPER_DEFAULTS = dict(I0=24, alpha=1, n_rnd=12, jperp_min=0, jperp_max=6, beta=3, tau=100, delay=1,
+                      coupling=COUPLING_UPPER, init_mode=INIT_RANDOM, algo=ALGO_AUTO)
+
+
+def make_params(*, R: int, cycles: int, trials: int, seed: int, **kw) -> Params:
+    p = Params()
+    lib().ssqa_params_default(ctypes.byref(p))
+    p.R, p.cycles, p.trials, p.seed = R, cycles, trials, seed
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_best: bool = False,
+           state=None, want_hist: bool = False, stream=None, **kw):
+    """Anneal with host buffers; returns numpy arrays (sigma, Is, E_final, ...)."""
+    N = ising.N
+    p = make_params(R=R, cycles=cycles, trials=trials, seed=seed, **kw)
+    if track_best:
+        p.flags |= FLAG_TRACK_BEST
+    d = p.delay
+    sigma = np.zeros((trials, R, N), np.int8)
+    Is = np.zeros((trials, R, N), np.int32)
+    hist = np.zeros((trials, d, R, N), np.int8) if (d and (want_hist or state is not None)) else None
+    if state is not None:
+        sigma[...] = state["sigma"]
+        Is[...] = state["Is"]
+        if hist is not None:
+            hist[...] = state["hist"]
+    E = np.zeros((trials, R), np.int64)
+    Eb = np.zeros((trials, R), np.int64) if track_best else None
+    bc = np.zeros((trials, R), np.int32) if track_best else None
+    r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(E), _ptr(Eb), _ptr(bc))
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().ssqa_anneal(ising.handle, ctypes.byref(p), ctypes.byref(r), st), "anneal")
+    out = dict(sigma=sigma, Is=Is, E_final=E)
+    if hist is not None:
+        out["hist"] = hist
+    if track_best:
+        out.update(E_best=Eb, best_cycle=bc)
+    return out
+
+
+def anneal_device(ising: Ising, params: Params, sigma, Is, e_final=None, hist=None, e_best=None, best_cycle=None,
+                  stream=None):
+    """Anneal on device buffers (torch CUDA tensors); enqueued on `stream`
+    (a torch.cuda.Stream or raw handle, default: torch's current stream)."""
+    import torch
+
+    p = Params.from_buffer_copy(params)
+    p.flags |= FLAG_DEVICE_PTRS
+    if e_best is not None:
+        p.flags |= FLAG_TRACK_BEST
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(e_final), _ptr(e_best), _ptr(best_cycle))
+    _check(lib().ssqa_anneal(ising.handle, ctypes.byref(p), ctypes.byref(r), ctypes.c_void_p(handle)), "anneal")
+
+
+def energy(ising: Ising, sigma) -> np.ndarray:
+    s = np.ascontiguousarray(sigma, np.int8)
+    N = ising.N
+    flat = s.reshape(-1, N)
+    E = np.zeros(flat.shape[0], np.int64)
+    _check(lib().ssqa_energy(ising.handle, _ptr(flat), flat.shape[0], _ptr(E), 0, None), "energy")
+    return E.reshape(s.shape[:-1])
+
+
+def tts(t: float, p_s: float, p_target: float = 0.99) -> float:
+    return float(lib().ssqa_tts(t, p_s, p_target))

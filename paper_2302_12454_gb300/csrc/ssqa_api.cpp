@@ -1,0 +1,602 @@
+// C ABI of the SSQA library: argument checking, instance construction
+// (Sec. 4.1-4.2 of the paper), device copies, and dispatch of the anneal to
+// the CUDA kernels.  Every step of an anneal runs on the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <new>
+#include <numeric>
+
+#include "ssqa_internal.h"
+
+namespace ssqa {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int check_device(int *device) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SSQA_ERR_DEVICE, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    int major = 0;
+    e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (e != cudaSuccess || major != 10)
+        return fail(SSQA_ERR_DEVICE, "the library is built for sm_103a (compute capability 10.x)");
+    if (device) *device = dev;
+    return SSQA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea, Flood 2014): Weyl step then the 64-bit finaliser.
+// ---------------------------------------------------------------------------
+namespace {
+struct SplitMix64 {
+    uint64_t s;
+    explicit SplitMix64(uint64_t seed) : s(seed) {}
+    uint64_t next() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    // uniform in [0, m): top 32 bits, rejecting the biased tail of 2^32
+    uint32_t below(uint32_t m) {
+        const uint64_t lim = (uint64_t(1) << 32) - ((uint64_t(1) << 32) % m);
+        for (;;) {
+            uint64_t x = next() >> 32;
+            if (x < lim) return uint32_t(x % m);
+        }
+    }
+};
+
+// FP8 E4M3 (OCP "FN" variant: bias 7, no infinities) encoding of an integer,
+// or -1 if it has no exact E4M3 value.
+int e4m3_of_int(int64_t v) {
+    if (v == 0) return 0;
+    int sign = v < 0 ? 0x80 : 0;
+    uint64_t a = uint64_t(v < 0 ? -v : v);
+    if (a > 448) return -1;
+    int e = 63 - __builtin_clzll(a);     // a in [2^e, 2^(e+1))
+    uint64_t frac = a - (uint64_t(1) << e);  // mantissa bits: frac / 2^e * 8
+    if (e >= 3) {
+        if (frac % (uint64_t(1) << (e - 3))) return -1;
+        frac >>= (e - 3);
+    } else {
+        frac <<= (3 - e);
+    }
+    int biased = e + 7;
+    if (biased > 15 || (biased == 15 && frac == 7)) return -1;
+    return sign | (biased << 3) | int(frac);
+}
+
+int64_t gcd64(int64_t a, int64_t b) {
+    a = a < 0 ? -a : a;
+    b = b < 0 ? -b : b;
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Build the tcgen05 operand image of an instance (see TcImage).
+void prepare_tc(ssqa_ising *I) {
+    TcImage &t = I->tc;
+    const int N = I->N;
+    int64_t g = 0;
+    for (int8_t v : I->J) g = gcd64(g, v);
+    for (int32_t v : I->h) g = gcd64(g, v);
+    if (g == 0) g = 1;
+    if (g > 2048) {
+        t.why = "common factor of J and h too large for the FP16 epilogue";
+        return;
+    }
+    t.jm = int32_t(g);
+    t.h_unit.resize(N);
+    int64_t hmax = 0;
+    for (int i = 0; i < N; ++i) {
+        t.h_unit[i] = int32_t(I->h[i] / g);
+        hmax = std::max<int64_t>(hmax, std::llabs(t.h_unit[i]));
+    }
+    // h digit columns: weights 1, 16, then 256 repeated
+    int nh;
+    if (hmax == 0) nh = 0;
+    else if (hmax < 16) nh = 1;
+    else if (hmax < 256) nh = 2;
+    else nh = 2 + int((hmax / 256 + 14) / 15);
+    t.nh = nh;
+    t.N16 = (N + 15) / 16 * 16;
+    t.Kp = (t.N16 + nh + 31) / 32 * 32;
+    if (N <= 256) {
+        t.nchunk = 1;
+        t.chunk_rows[0] = t.N16;
+    } else if (N <= 512) {
+        t.nchunk = 2;
+        t.chunk_rows[0] = 256;
+        t.chunk_rows[1] = (N - 256 + 15) / 16 * 16;
+    } else {
+        t.why = "N > 512 needs more tensor memory than one CTA holds";
+        return;
+    }
+    t.Brows = t.chunk_rows[0] + t.chunk_rows[1];
+    // accumulator bound: every partial sum of D stays an exact small integer
+    for (int i = 0; i < N; ++i) {
+        int64_t s = std::llabs(t.h_unit[i]);
+        for (int j = 0; j < N; ++j) s += std::llabs(I->J[size_t(i) * N + j] / g);
+        if (s > 16384) {
+            t.why = "row sums of |J|/jm + |h|/jm exceed 2^14";
+            return;
+        }
+    }
+    const int Kp = t.Kp;
+    auto off = [Kp](int r, int k) -> size_t {
+        return size_t(r / 8) * (size_t(Kp) * 8) + size_t(k / 16) * 128 + size_t(r % 8) * 16 + size_t(k % 16);
+    };
+    t.b.assign(size_t(t.Brows) * Kp, 0);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            int8_t v = I->J[size_t(i) * N + j];
+            if (!v) continue;
+            int code = e4m3_of_int(v / g);
+            if (code < 0) {
+                t.why = "a coupling J/jm has no exact FP8 E4M3 value";
+                t.b.clear();
+                return;
+            }
+            t.b[off(i, j)] = uint8_t(code);
+        }
+    t.a_w.assign(nh, 0);
+    for (int m = 0; m < nh; ++m) t.a_w[m] = uint8_t(e4m3_of_int(m == 0 ? 1 : (m == 1 ? 16 : 256)));
+    for (int i = 0; i < N; ++i) {
+        int64_t hv = t.h_unit[i];
+        int sgn = hv < 0 ? -1 : 1;
+        int64_t a = std::llabs(hv);
+        for (int m = 0; m < nh; ++m) {
+            int64_t d;
+            if (m == 0) d = a % 16;
+            else if (m == 1) d = (a / 16) % 16;
+            else {
+                int64_t rest = a / 256 - int64_t(m - 2) * 15;
+                d = std::max<int64_t>(0, std::min<int64_t>(15, rest));
+            }
+            t.b[off(i, t.N16 + m)] = uint8_t(e4m3_of_int(sgn * d));
+        }
+    }
+    t.ok = true;
+}
+
+ssqa_ising *new_ising(int32_t N) {
+    ssqa_ising *I = new (std::nothrow) ssqa_ising();
+    if (!I) return nullptr;
+    try {
+        I->N = N;
+        I->J.assign(size_t(N) * N, 0);
+        I->h.assign(N, 0);
+    } catch (...) {
+        delete I;
+        return nullptr;
+    }
+    return I;
+}
+}  // namespace
+
+int device_copy(const ssqa_ising *cI, DeviceCopy **out) {
+    ssqa_ising *I = const_cast<ssqa_ising *>(cI);
+    int dev = 0;
+    int rc = check_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(I->mu);
+    auto it = I->dev.find(dev);
+    if (it != I->dev.end()) {
+        *out = &it->second;
+        return SSQA_OK;
+    }
+    DeviceCopy dc;
+    const size_t N = size_t(I->N);
+    auto bad = [&](cudaError_t e) {
+        cudaFree(dc.J);
+        cudaFree(dc.J_pad);
+        cudaFree(dc.h);
+        cudaFree(dc.tc_b);
+        cudaFree(dc.tc_h_unit);
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SSQA_ERR_OOM : SSQA_ERR_DEVICE,
+                    std::string("instance upload: ") + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&dc.J, N * N))) return bad(e);
+    if ((e = cudaMalloc(&dc.h, N * 4))) return bad(e);
+    if ((e = cudaMemcpy(dc.J, I->J.data(), N * N, cudaMemcpyHostToDevice))) return bad(e);
+    dc.Np = int32_t((N + 15) / 16 * 16);
+    if ((e = cudaMalloc(&dc.J_pad, N * dc.Np))) return bad(e);
+    if ((e = cudaMemset(dc.J_pad, 0, N * dc.Np))) return bad(e);
+    if ((e = cudaMemcpy2D(dc.J_pad, dc.Np, I->J.data(), N, N, N, cudaMemcpyHostToDevice))) return bad(e);
+    if ((e = cudaMemcpy(dc.h, I->h.data(), N * 4, cudaMemcpyHostToDevice))) return bad(e);
+    if (I->tc.ok) {
+        if ((e = cudaMalloc(&dc.tc_b, I->tc.b.size()))) return bad(e);
+        if ((e = cudaMemcpy(dc.tc_b, I->tc.b.data(), I->tc.b.size(), cudaMemcpyHostToDevice))) return bad(e);
+        if ((e = cudaMalloc(&dc.tc_h_unit, N * 4))) return bad(e);
+        if ((e = cudaMemcpy(dc.tc_h_unit, I->tc.h_unit.data(), N * 4, cudaMemcpyHostToDevice))) return bad(e);
+    }
+    auto res = I->dev.emplace(dev, dc);
+    *out = &res.first->second;
+    return SSQA_OK;
+}
+
+}  // namespace ssqa
+
+using namespace ssqa;
+
+extern "C" {
+
+const char *ssqa_last_error(void) { return g_last_error.c_str(); }
+
+int ssqa_gen_er_graph(int32_t n, uint32_t p_q32, uint64_t seed, uint8_t *adj) {
+    if (n < 1 || n > 65535 || !adj) return fail(SSQA_ERR_INVALID_ARG, "ssqa_gen_er_graph: bad n or adj");
+    SplitMix64 rng(seed);
+    for (int32_t i = 0; i < n; ++i) adj[size_t(i) * n + i] = 0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = i + 1; j < n; ++j) {
+            const uint8_t e = (rng.next() >> 32) < p_q32 ? 1 : 0;
+            adj[size_t(i) * n + j] = e;
+            adj[size_t(j) * n + i] = e;
+        }
+    return SSQA_OK;
+}
+
+int ssqa_permute_graph(int32_t n, const uint8_t *adj, uint64_t seed, uint8_t *adj_out, int32_t *perm_out) {
+    if (n < 1 || n > 65535 || !adj || !adj_out || !perm_out)
+        return fail(SSQA_ERR_INVALID_ARG, "ssqa_permute_graph: bad arguments");
+    std::vector<int32_t> pi(n);
+    std::iota(pi.begin(), pi.end(), 0);
+    SplitMix64 rng(seed);
+    for (int32_t i = n - 1; i >= 1; --i) std::swap(pi[i], pi[rng.below(uint32_t(i) + 1)]);
+    for (int32_t u = 0; u < n; ++u) {
+        perm_out[u] = pi[u];
+        for (int32_t v = 0; v < n; ++v) adj_out[size_t(pi[u]) * n + pi[v]] = adj[size_t(u) * n + v];
+    }
+    return SSQA_OK;
+}
+
+int ssqa_build_gi_ising(int32_t n, const uint8_t *adj1, const uint8_t *adj2, int32_t C1, int32_t C2,
+                        int32_t scale, ssqa_ising **out) {
+    if (!out) return fail(SSQA_ERR_INVALID_ARG, "ssqa_build_gi_ising: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 181 || !adj1 || !adj2 || C1 < 1 || C2 < 1 || scale < 1)
+        return fail(SSQA_ERR_INVALID_ARG, "ssqa_build_gi_ising: bad n, graph, penalties or scale");
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < n; ++j) {
+            const size_t a = size_t(i) * n + j, b = size_t(j) * n + i;
+            if (adj1[a] > 1 || adj2[a] > 1 || adj1[a] != adj1[b] || adj2[a] != adj2[b] ||
+                (i == j && (adj1[a] || adj2[a])))
+                return fail(SSQA_ERR_INVALID_ARG, "ssqa_build_gi_ising: graphs must be 0/1, symmetric, loop-free");
+        }
+    const int32_t N = n * n;
+    // Q of Eq. 7 from Eq. 8, per unordered spin pair {a = (u,i), b = (v,j)}:
+    //   same u, i != j  : 2 C1           (square of the row one-hot term)
+    //   same i, u != v  : 2 C1           (square of the column one-hot term)
+    //   u != v, i != j  : 2 C2 if edge(i,j in G1) != edge(u,v in G2)
+    //                     (each mismatch appears as two ordered pairs)
+    //   diagonal Q_aa   : -2 C1,  constant 2 n C1.
+    // Ising (Sec. 4.2): J_ab = -Q_ab / 4, h_a = -Q_aa/2 - sum_b Q_ab / 4.
+    // Everything is carried times 4 and divided by 4 once, after scaling.
+    std::unique_ptr<ssqa_ising> I(new_ising(N));
+    if (!I) return fail(SSQA_ERR_OOM, "ssqa_build_gi_ising: out of host memory");
+    const int64_t S = scale;
+    int64_t off4 = 4 * int64_t(2) * n * C1;  // 4 * constant
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t a = u * n + i;
+            const int64_t qaa = -2 * int64_t(C1);
+            int64_t h4 = -2 * qaa;  // 4 * (-Q_aa / 2)
+            off4 += 2 * qaa;        // 4 * Q_aa / 2
+            for (int32_t v = 0; v < n; ++v)
+                for (int32_t j = 0; j < n; ++j) {
+                    const int32_t b = v * n + j;
+                    if (b == a) continue;
+                    int64_t q = 0;
+                    if (u == v) q = 2 * int64_t(C1);
+                    else if (i == j) q = 2 * int64_t(C1);
+                    else if (adj1[size_t(i) * n + j] != adj2[size_t(u) * n + v]) q = 2 * int64_t(C2);
+                    if (!q) continue;
+                    h4 -= q;
+                    if (b > a) off4 += q;
+                    const int64_t j4 = -S * q;
+                    if (j4 % 4 || j4 / 4 < -127 || j4 / 4 > 127)
+                        return fail(SSQA_ERR_INVALID_ARG, "ssqa_build_gi_ising: scaled J not an int8 integer");
+                    I->J[size_t(a) * N + b] = int8_t(j4 / 4);
+                }
+            const int64_t hs = S * h4;
+            if (hs % 4 || hs / 4 < INT32_MIN || hs / 4 > INT32_MAX)
+                return fail(SSQA_ERR_INVALID_ARG, "ssqa_build_gi_ising: scaled h not an int32 integer");
+            I->h[a] = int32_t(hs / 4);
+        }
+    if ((S * off4) % 4) return fail(SSQA_ERR_INVALID_ARG, "ssqa_build_gi_ising: scaled offset not an integer");
+    I->e_offset = S * off4 / 4;
+    prepare_tc(I.get());
+    *out = I.release();
+    return SSQA_OK;
+}
+
+int ssqa_ising_from_dense(int32_t N, const int8_t *J, const int32_t *h, int64_t e_offset, ssqa_ising **out) {
+    if (!out) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > 65536 || !J || !h) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: bad N, J or h");
+    for (int32_t i = 0; i < N; ++i) {
+        if (J[size_t(i) * N + i]) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: J diagonal must be 0");
+        for (int32_t j = i + 1; j < N; ++j)
+            if (J[size_t(i) * N + j] != J[size_t(j) * N + i])
+                return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: J must be symmetric");
+    }
+    std::unique_ptr<ssqa_ising> I(new_ising(N));
+    if (!I) return fail(SSQA_ERR_OOM, "ssqa_ising_from_dense: out of host memory");
+    std::memcpy(I->J.data(), J, size_t(N) * N);
+    std::memcpy(I->h.data(), h, size_t(N) * 4);
+    I->e_offset = e_offset;
+    prepare_tc(I.get());
+    *out = I.release();
+    return SSQA_OK;
+}
+
+void ssqa_ising_free(ssqa_ising *I) {
+    if (!I) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : I->dev) {
+        cudaSetDevice(kv.first);
+        cudaFree(kv.second.J);
+        cudaFree(kv.second.J_pad);
+        cudaFree(kv.second.h);
+        cudaFree(kv.second.tc_b);
+        cudaFree(kv.second.tc_h_unit);
+    }
+    cudaSetDevice(cur);
+    cudaGetLastError();
+    delete I;
+}
+
+int ssqa_ising_export(const ssqa_ising *I, int32_t *N, int64_t *e_offset, int32_t *h, int8_t *J) {
+    if (!I) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_export: NULL instance");
+    if (N) *N = I->N;
+    if (e_offset) *e_offset = I->e_offset;
+    if (h) std::memcpy(h, I->h.data(), size_t(I->N) * 4);
+    if (J) std::memcpy(J, I->J.data(), size_t(I->N) * I->N);
+    return SSQA_OK;
+}
+
+void ssqa_params_default(ssqa_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->R = 25;
+    p->cycles = 0;
+    p->trials = 1;
+    p->I0 = 24;
+    p->alpha = 1;
+    p->n_rnd = 12;
+    p->jperp_min = 0;
+    p->jperp_max = 6;
+    p->beta = 3;
+    p->tau = 100;
+    p->delay = 1;
+    p->coupling = SSQA_COUPLING_UPPER;
+    p->init_mode = SSQA_INIT_RANDOM;
+    p->algo = SSQA_ALGO_AUTO;
+}
+
+double ssqa_tts(double t, double p_s, double p_target) {
+    if (!(p_target > 0.0 && p_target < 1.0)) return std::numeric_limits<double>::quiet_NaN();
+    if (p_s >= 1.0) return 0.0;
+    if (p_s <= 0.0) return std::numeric_limits<double>::infinity();
+    return t * std::log1p(-p_target) / std::log1p(-p_s);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// anneal / energy dispatch
+// ---------------------------------------------------------------------------
+namespace {
+
+int validate(const ssqa_ising *I, const ssqa_params *p, const ssqa_result *r) {
+    if (!I || !p || !r) return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal: NULL argument");
+    if (p->R < 1 || p->R > 128) return fail(SSQA_ERR_INVALID_ARG, "R must be in 1..128");
+    if (p->trials < 1 || p->cycles < 0) return fail(SSQA_ERR_INVALID_ARG, "trials >= 1 and cycles >= 0 required");
+    if (int64_t(p->trials) * p->R > (int64_t(1) << 30) ||
+        int64_t(p->trials) * p->R * I->N > (int64_t(1) << 40))
+        return fail(SSQA_ERR_INVALID_ARG, "trials * R * N too large");
+    if (p->I0 < 1 || p->I0 > 16383) return fail(SSQA_ERR_INVALID_ARG, "I0 must be in 1..16383");
+    if (p->alpha < 1 || p->alpha > 2 * p->I0) return fail(SSQA_ERR_INVALID_ARG, "alpha must be in 1..2*I0");
+    if (p->n_rnd < 0 || p->n_rnd > (1 << 20)) return fail(SSQA_ERR_INVALID_ARG, "n_rnd out of range");
+    if (p->beta < 1 || p->tau < 1) return fail(SSQA_ERR_INVALID_ARG, "beta and tau must be >= 1");
+    if (std::abs(int64_t(p->jperp_min)) > (1 << 20) || std::abs(int64_t(p->jperp_max)) > (1 << 20))
+        return fail(SSQA_ERR_INVALID_ARG, "jperp out of range");
+    if ((int64_t(p->jperp_max) - p->jperp_min) % p->beta)
+        return fail(SSQA_ERR_INVALID_ARG, "(jperp_max - jperp_min) must be divisible by beta");
+    if (p->delay < 0 || p->delay > 3) return fail(SSQA_ERR_INVALID_ARG, "delay must be in 0..3");
+    if (p->coupling != SSQA_COUPLING_UPPER && p->coupling != SSQA_COUPLING_BOTH)
+        return fail(SSQA_ERR_INVALID_ARG, "unknown coupling mode");
+    if (p->init_mode < 0 || p->init_mode > 2) return fail(SSQA_ERR_INVALID_ARG, "unknown init mode");
+    if (p->algo < 0 || p->algo > 2) return fail(SSQA_ERR_INVALID_ARG, "unknown algo");
+    if (p->start_cycle < 0 || int64_t(p->start_cycle) + p->cycles > 0xFFFFFFFEll)
+        return fail(SSQA_ERR_INVALID_ARG, "cycle range must stay below 2^32 - 1");
+    if (int64_t(p->trial_offset) + p->trials > 0xFFFFFFFFll)
+        return fail(SSQA_ERR_INVALID_ARG, "trial_offset + trials must fit 32 bits");
+    if (!r->sigma || !r->is_state) return fail(SSQA_ERR_INVALID_ARG, "sigma and is_state buffers are required");
+    if (p->init_mode == SSQA_INIT_FROM_STATE && p->delay > 0 && !r->sigma_hist)
+        return fail(SSQA_ERR_INVALID_ARG, "resuming with delay > 0 needs sigma_hist");
+    if ((p->flags & SSQA_FLAG_TRACK_BEST) && (!r->e_best || !r->best_cycle))
+        return fail(SSQA_ERR_INVALID_ARG, "TRACK_BEST needs e_best and best_cycle");
+    if (p->flags & ~(SSQA_FLAG_TRACK_BEST | SSQA_FLAG_DEVICE_PTRS))
+        return fail(SSQA_ERR_INVALID_ARG, "unknown flag bits");
+    return SSQA_OK;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+int cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? SSQA_ERR_OOM : SSQA_ERR_DEVICE,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_result *r, void *stream) {
+    int rc = validate(I, p, r);
+    if (rc) return rc;
+    DeviceCopy *dc = nullptr;
+    if ((rc = device_copy(I, &dc))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool devptr = p->flags & SSQA_FLAG_DEVICE_PTRS;
+    const size_t cols = size_t(p->trials) * p->R;
+    const size_t nsp = cols * I->N;
+    const int d = p->delay;
+
+    AnnealArgs a{};
+    a.N = I->N;
+    a.R = p->R;
+    a.trials = p->trials;
+    a.cycles = p->cycles;
+    a.I0 = p->I0;
+    a.alpha = p->alpha;
+    a.n_rnd = p->n_rnd;
+    a.jperp_min = p->jperp_min;
+    a.jperp_step = (p->jperp_max - p->jperp_min) / p->beta;
+    a.beta = p->beta;
+    a.tau = p->tau;
+    a.delay = d;
+    a.both = p->coupling == SSQA_COUPLING_BOTH;
+    a.init_mode = p->init_mode;
+    a.start_cycle = p->start_cycle;
+    a.trial_offset = p->trial_offset;
+    a.seed = p->seed;
+    a.track_best = p->flags & SSQA_FLAG_TRACK_BEST;
+    a.J = dc->J;
+    a.J_pad = dc->J_pad;
+    a.Np = dc->Np;
+    a.h = dc->h;
+
+    // state / result buffers on the device
+    DevBuf b_sig, b_hist, b_is, b_ef, b_eb, b_bc;
+    auto alloc = [&](DevBuf &b, size_t bytes) -> cudaError_t {
+        b.s = st;
+        return cudaMallocAsync(&b.p, bytes ? bytes : 1, st);
+    };
+    cudaError_t e;
+    if (devptr) {
+        a.sigma = r->sigma;
+        a.hist = d ? r->sigma_hist : nullptr;
+        a.Is = r->is_state;
+        a.e_final = r->e_final;
+        a.e_best = a.track_best ? r->e_best : nullptr;
+        a.best_cycle = a.track_best ? r->best_cycle : nullptr;
+    } else {
+        if ((e = alloc(b_sig, nsp))) return cuda_fail(e, "ssqa_anneal: state allocation");
+        if ((e = alloc(b_is, nsp * 4))) return cuda_fail(e, "ssqa_anneal: state allocation");
+        a.sigma = static_cast<int8_t *>(b_sig.p);
+        a.Is = static_cast<int32_t *>(b_is.p);
+        if (d && (r->sigma_hist || p->init_mode == SSQA_INIT_FROM_STATE)) {
+            if ((e = alloc(b_hist, nsp * d))) return cuda_fail(e, "ssqa_anneal: state allocation");
+            a.hist = static_cast<int8_t *>(b_hist.p);
+        }
+        if (r->e_final) {
+            if ((e = alloc(b_ef, cols * 8))) return cuda_fail(e, "ssqa_anneal: result allocation");
+            a.e_final = static_cast<int64_t *>(b_ef.p);
+        }
+        if (a.track_best) {
+            if ((e = alloc(b_eb, cols * 8))) return cuda_fail(e, "ssqa_anneal: result allocation");
+            if ((e = alloc(b_bc, cols * 4))) return cuda_fail(e, "ssqa_anneal: result allocation");
+            a.e_best = static_cast<int64_t *>(b_eb.p);
+            a.best_cycle = static_cast<int32_t *>(b_bc.p);
+        }
+        if (p->init_mode == SSQA_INIT_FROM_STATE) {
+            if ((e = cudaMemcpyAsync(a.sigma, r->sigma, nsp, cudaMemcpyHostToDevice, st)) ||
+                (e = cudaMemcpyAsync(a.Is, r->is_state, nsp * 4, cudaMemcpyHostToDevice, st)))
+                return cuda_fail(e, "ssqa_anneal: state upload");
+            if (d && (e = cudaMemcpyAsync(a.hist, r->sigma_hist, nsp * d, cudaMemcpyHostToDevice, st)))
+                return cuda_fail(e, "ssqa_anneal: state upload");
+        }
+    }
+
+    std::string why;
+    bool use_tc = false;
+    if (p->algo == SSQA_ALGO_TENSOR) {
+        if (!tc_supported(I->tc, a, &why)) return fail(SSQA_ERR_UNSUPPORTED, "tensor path: " + why);
+        use_tc = true;
+    } else if (p->algo == SSQA_ALGO_AUTO) {
+        use_tc = tc_supported(I->tc, a, &why);
+    }
+    if (use_tc) {
+        rc = tc_anneal(I->tc, *dc, a, st);
+    } else {
+        DevBuf scratch;
+        if ((e = alloc(scratch, plain_scratch_bytes(a)))) return cuda_fail(e, "ssqa_anneal: scratch allocation");
+        rc = plain_anneal(a, scratch.p, st);
+    }
+    if (rc) return rc;
+    if (!devptr) {
+        if ((e = cudaMemcpyAsync(r->sigma, a.sigma, nsp, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(r->is_state, a.Is, nsp * 4, cudaMemcpyDeviceToHost, st)))
+            return cuda_fail(e, "ssqa_anneal: result download");
+        if (r->sigma_hist && a.hist &&
+            (e = cudaMemcpyAsync(r->sigma_hist, a.hist, nsp * d, cudaMemcpyDeviceToHost, st)))
+            return cuda_fail(e, "ssqa_anneal: result download");
+        if (r->e_final && (e = cudaMemcpyAsync(r->e_final, a.e_final, cols * 8, cudaMemcpyDeviceToHost, st)))
+            return cuda_fail(e, "ssqa_anneal: result download");
+        if (a.track_best &&
+            ((e = cudaMemcpyAsync(r->e_best, a.e_best, cols * 8, cudaMemcpyDeviceToHost, st)) ||
+             (e = cudaMemcpyAsync(r->best_cycle, a.best_cycle, cols * 4, cudaMemcpyDeviceToHost, st))))
+            return cuda_fail(e, "ssqa_anneal: result download");
+        if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "ssqa_anneal");
+    }
+    if ((e = cudaGetLastError())) return cuda_fail(e, "ssqa_anneal");
+    return SSQA_OK;
+}
+
+extern "C" int ssqa_energy(const ssqa_ising *I, const int8_t *sigma, int64_t count, int64_t *E_out, uint32_t flags,
+                           void *stream) {
+    if (!I || !sigma || !E_out || count < 0) return fail(SSQA_ERR_INVALID_ARG, "ssqa_energy: bad arguments");
+    if (flags & ~uint32_t(SSQA_FLAG_DEVICE_PTRS)) return fail(SSQA_ERR_INVALID_ARG, "ssqa_energy: unknown flags");
+    if (count == 0) return SSQA_OK;
+    DeviceCopy *dc = nullptr;
+    int rc = device_copy(I, &dc);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (flags & SSQA_FLAG_DEVICE_PTRS)
+        return energy_launch(dc->J_pad, dc->Np, dc->h, I->N, sigma, I->N, count, E_out, st);
+    DevBuf bs, be;
+    bs.s = be.s = st;
+    const size_t nb = size_t(count) * I->N;
+    if ((e = cudaMallocAsync(&bs.p, nb, st)) || (e = cudaMallocAsync(&be.p, size_t(count) * 8, st)))
+        return cuda_fail(e, "ssqa_energy: allocation");
+    if ((e = cudaMemcpyAsync(bs.p, sigma, nb, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "ssqa_energy: upload");
+    rc = energy_launch(dc->J_pad, dc->Np, dc->h, I->N, static_cast<int8_t *>(bs.p), I->N, count,
+                       static_cast<int64_t *>(be.p), st);
+    if (rc) return rc;
+    if ((e = cudaMemcpyAsync(E_out, be.p, size_t(count) * 8, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return cuda_fail(e, "ssqa_energy: download");
+    return SSQA_OK;
+}

@@ -1,0 +1,114 @@
+// Internal declarations shared by the host side (ssqa_api.cpp, ssqa_server.cpp)
+// and the CUDA kernels (ssqa_plain.cu, ssqa_tc.cu) of the SSQA library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ssqa.h"
+
+namespace ssqa {
+
+// Record an error for ssqa_last_error() and return `code`.
+int fail(int code, const std::string &msg);
+
+// ---------------------------------------------------------------------------
+// Tensor-core operand image of an instance.  The field product of Eq. 6a,
+// F_{i,c} = sum_j J_ij sigma_{j,c}, runs as D = A * B^T on tcgen05 with
+//   A[c][j] = sigma_{j,c}           (128 columns c = trial*R + k of one CTA)
+//   B[i][j] = J_ij / jm             (spin rows i, FP8 E4M3, exact small ints)
+// plus `nh` extra K columns that add h_i / jm:  A[c][N16 + m] = weight_m,
+// B[i][N16 + m] = digit_m(h_i / jm), weights 1, 16, 256, 256, ...
+// so D_{c,i} = (F_{i,c} + h_i) / jm exactly.  Both operands use the
+// no-swizzle K-major core-matrix layout: element (r, k) at byte
+//   (r / 8) * (Kp * 8) + (k / 16) * 128 + (r % 8) * 16 + (k % 16).
+// ---------------------------------------------------------------------------
+struct TcImage {
+    bool ok = false;          // instance representable exactly on this path
+    std::string why;          // reason when !ok
+    int32_t jm = 1;           // common factor of J' and h'
+    int32_t N16 = 0;          // N rounded up to 16
+    int32_t nh = 0;           // number of h digit columns
+    int32_t Kp = 0;           // K extent (multiple of 32)
+    int32_t nchunk = 0;       // MMA N-chunks (<= 2)
+    int32_t chunk_rows[2] = {0, 0};
+    int32_t Brows = 0;        // sum of chunk rows
+    std::vector<uint8_t> b;   // B image, Brows * Kp bytes
+    std::vector<uint8_t> a_w; // e4m3 weights of the h columns (nh bytes)
+    std::vector<int32_t> h_unit; // h_i / jm (N)
+};
+
+struct DeviceCopy {
+    int8_t *J = nullptr;       // N*N int8
+    int8_t *J_pad = nullptr;   // N rows of Np bytes (zero padded), plain path
+    int32_t Np = 0;            // N rounded up to 16
+    int32_t *h = nullptr;      // N int32
+    uint8_t *tc_b = nullptr;   // B image
+    int32_t *tc_h_unit = nullptr;
+};
+
+}  // namespace ssqa
+
+struct ssqa_ising {
+    int32_t N = 0;
+    std::vector<int8_t> J;     // N*N
+    std::vector<int32_t> h;    // N
+    int64_t e_offset = 0;
+    ssqa::TcImage tc;
+    std::mutex mu;
+    std::map<int, ssqa::DeviceCopy> dev;  // per CUDA device
+};
+
+namespace ssqa {
+
+// Device copy of an instance on the current device (created on first use).
+int device_copy(const ssqa_ising *ising, DeviceCopy **out);
+
+// ---------------------------------------------------------------------------
+// Launch descriptors (device pointers only)
+// ---------------------------------------------------------------------------
+struct AnnealArgs {
+    int32_t N, R, trials, cycles;
+    int32_t I0, alpha, n_rnd;
+    int32_t jperp_min, jperp_step, beta, tau;
+    int32_t delay, both, init_mode, start_cycle;
+    uint32_t trial_offset;
+    uint64_t seed;
+    bool track_best;
+    // instance
+    const int8_t *J;
+    const int8_t *J_pad;  // rows padded to Np bytes
+    int32_t Np;
+    const int32_t *h;
+    // state / results (device)
+    int8_t *sigma;        // [cols][N]   in (resume) / out
+    int8_t *hist;         // [trials][d][R][N] in/out (may be null if d == 0)
+    int32_t *Is;          // [cols][N]   in/out
+    int64_t *e_final;     // [cols] or null
+    int64_t *e_best;      // [cols] or null
+    int32_t *best_cycle;  // [cols] or null
+};
+
+// Bytes of scratch the plain path needs for `a` (see plain_anneal).
+size_t plain_scratch_bytes(const AnnealArgs &a);
+// Plain CUDA-core path: one launch per cycle.  `scratch` must hold
+// plain_scratch_bytes(a) bytes of device memory (256-byte aligned).
+int plain_anneal(const AnnealArgs &a, void *scratch, void *stream);
+
+// Energy E' of `count` spin rows of `pitch` bytes (device pointers), using
+// the zero-padded J rows (pitch Np).  No scratch.
+int energy_launch(const int8_t *J_pad, int32_t Np, const int32_t *h, int32_t N, const int8_t *sigma,
+                  int64_t pitch, int64_t count, int64_t *E, void *stream);
+
+// Tensor-core path: whether the resident kernel can run this problem.
+bool tc_supported(const TcImage &img, const AnnealArgs &a, std::string *why);
+int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream);
+
+// Current device has compute capability 10.x (sm_100 family).
+int check_device(int *device);
+
+}  // namespace ssqa

@@ -1,0 +1,238 @@
+// Continuous-batching server for SSQA anneals (ssqa_server_* / ssqa_submit /
+// ssqa_poll).  The paper runs one anneal at a time; serving many GI / Ising
+// solves of different sizes is this library's addition around the same
+// per-request computation (Eq. 6).
+//
+// Requests queue on the host.  `max_slots` worker threads each own a CUDA
+// stream; a worker admits the oldest queued request whose device footprint
+// fits in what is left of the HBM budget, runs it with ssqa_anneal on its
+// stream (all state device-resident for the whole anneal), and publishes the
+// result.  Requests admitted while others run overlap on the GPU.  Results
+// are identical to a lone ssqa_anneal call: every random draw is keyed by the
+// request's own seed and trial indices.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ssqa_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    const ssqa_ising *ising = nullptr;
+    ssqa_params params{};
+    size_t bytes = 0;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int rc = SSQA_OK;
+    std::string err;
+    std::vector<int8_t> sigma, hist;
+    std::vector<int32_t> is;
+    std::vector<int64_t> e_final, e_best;
+    std::vector<int32_t> best_cycle;
+    Clock::time_point t_submit, t_done;
+};
+
+size_t footprint(const ssqa_ising *I, const ssqa_params &p) {
+    const size_t N = size_t(I->N), cols = size_t(p.trials) * p.R;
+    const size_t state = cols * N * (1 + 4 + size_t(p.delay)) + cols * 24;
+    const size_t scratch = size_t(p.delay + 2) * cols * ((N + 15) / 16 * 16) + cols * 16;
+    const size_t instance = N * N * 2 + N * 8 + I->tc.b.size();
+    return state + scratch + instance;
+}
+
+}  // namespace
+
+struct ssqa_server {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::vector<std::thread> workers;
+
+    void worker() {
+        cudaSetDevice(device);
+        cudaStream_t st = nullptr;
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        for (;;) {
+            std::shared_ptr<Request> r;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                for (;;) {
+                    if (stop && queue.empty()) break;
+                    for (auto it = queue.begin(); it != queue.end(); ++it)
+                        if (used + (*it)->bytes <= budget) {
+                            r = *it;
+                            queue.erase(it);
+                            break;
+                        }
+                    if (r) break;
+                    cv_work.wait(lk);
+                }
+                if (!r) break;
+                used += r->bytes;
+                r->state = 1;
+            }
+            run(r.get(), st);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                used -= r->bytes;
+                r->state = 2;
+                r->t_done = Clock::now();
+            }
+            cv_done.notify_all();
+            cv_work.notify_all();
+        }
+        if (st) cudaStreamDestroy(st);
+    }
+
+    static void run(Request *r, cudaStream_t st) {
+        const ssqa_params &p = r->params;
+        const size_t N = size_t(r->ising->N), cols = size_t(p.trials) * p.R;
+        try {
+            r->sigma.assign(cols * N, 0);
+            r->is.assign(cols * N, 0);
+            r->e_final.assign(cols, 0);
+            if (p.delay) r->hist.assign(cols * N * size_t(p.delay), 0);
+            if (p.flags & SSQA_FLAG_TRACK_BEST) {
+                r->e_best.assign(cols, 0);
+                r->best_cycle.assign(cols, 0);
+            }
+        } catch (...) {
+            r->rc = SSQA_ERR_OOM;
+            r->err = "server: out of host memory for results";
+            return;
+        }
+        ssqa_result res{};
+        res.sigma = r->sigma.data();
+        res.is_state = r->is.data();
+        res.e_final = r->e_final.data();
+        res.sigma_hist = p.delay ? r->hist.data() : nullptr;
+        if (p.flags & SSQA_FLAG_TRACK_BEST) {
+            res.e_best = r->e_best.data();
+            res.best_cycle = r->best_cycle.data();
+        }
+        r->rc = ssqa_anneal(r->ising, &p, &res, st);
+        if (r->rc) r->err = ssqa_last_error();
+    }
+};
+
+extern "C" {
+
+int ssqa_server_create(size_t hbm_budget, int32_t max_slots, int32_t device, ssqa_server **out) {
+    if (!out) return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_server_create: out is NULL");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 64 || hbm_budget == 0)
+        return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_server_create: max_slots in 1..64 and a nonzero budget");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return ssqa::fail(SSQA_ERR_DEVICE, "ssqa_server_create: no such CUDA device");
+    }
+    ssqa_server *s = new (std::nothrow) ssqa_server();
+    if (!s) return ssqa::fail(SSQA_ERR_OOM, "ssqa_server_create: out of host memory");
+    s->device = device;
+    s->budget = hbm_budget;
+    try {
+        for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s] { s->worker(); });
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv_work.notify_all();
+        for (auto &t : s->workers) t.join();
+        delete s;
+        return ssqa::fail(SSQA_ERR_OOM, "ssqa_server_create: cannot start worker threads");
+    }
+    *out = s;
+    return SSQA_OK;
+}
+
+void ssqa_server_destroy(ssqa_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &t : s->workers) t.join();
+    delete s;
+}
+
+int ssqa_submit(ssqa_server *s, const ssqa_ising *ising, const ssqa_params *params, uint64_t *ticket) {
+    if (!s || !ising || !params || !ticket) return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_submit: NULL argument");
+    if (params->flags & SSQA_FLAG_DEVICE_PTRS)
+        return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_submit: results are returned in host memory");
+    if (params->init_mode == SSQA_INIT_FROM_STATE)
+        return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_submit: resuming from a state is not served");
+    if (params->R < 1 || params->R > 128 || params->trials < 1 || params->cycles < 0 || params->delay < 0 ||
+        params->delay > 3)
+        return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_submit: bad R, trials, cycles or delay");
+    auto r = std::make_shared<Request>();
+    r->ising = ising;
+    r->params = *params;
+    r->bytes = footprint(ising, *params);
+    if (r->bytes > s->budget)
+        return ssqa::fail(SSQA_ERR_BUDGET, "ssqa_submit: request needs more device memory than the whole budget");
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_submit: server is shutting down");
+        r->ticket = s->next_ticket++;
+        s->queue.push_back(r);
+        s->all.emplace(r->ticket, r);
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_one();
+    return SSQA_OK;
+}
+
+int ssqa_poll(ssqa_server *s, uint64_t ticket, ssqa_result *out, int32_t timeout_ms, double *latency_us) {
+    if (!s) return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_poll: NULL server");
+    std::shared_ptr<Request> r;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) return ssqa::fail(SSQA_ERR_NOT_FOUND, "ssqa_poll: unknown ticket");
+        r = it->second;
+        auto done = [&] { return r->state == 2; };
+        if (timeout_ms < 0)
+            s->cv_done.wait(lk, done);
+        else if (!done())
+            s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
+        if (r->state != 2) return SSQA_PENDING;
+        s->all.erase(ticket);
+    }
+    if (latency_us) *latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+    if (r->rc) return ssqa::fail(r->rc, r->err);
+    if (out) {
+        const ssqa_params &p = r->params;
+        if (out->sigma) std::memcpy(out->sigma, r->sigma.data(), r->sigma.size());
+        if (out->is_state) std::memcpy(out->is_state, r->is.data(), r->is.size() * 4);
+        if (out->e_final) std::memcpy(out->e_final, r->e_final.data(), r->e_final.size() * 8);
+        if (out->sigma_hist && p.delay) std::memcpy(out->sigma_hist, r->hist.data(), r->hist.size());
+        if ((p.flags & SSQA_FLAG_TRACK_BEST) && out->e_best && out->best_cycle) {
+            std::memcpy(out->e_best, r->e_best.data(), r->e_best.size() * 8);
+            std::memcpy(out->best_cycle, r->best_cycle.data(), r->best_cycle.size() * 4);
+        }
+    }
+    return SSQA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,171 @@
+// Host side of the persistent tensor-core path: feasibility check, shared
+// memory plan, kernel parameters and launch (the kernel is in
+// ssqa_tc_kernel.cuh).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "ssqa_tc_kernel.cuh"
+
+namespace ssqa {
+namespace {
+using namespace tc;
+
+KernelFn pick(int d, bool both, bool track, bool alpha1) {
+    switch (d) {
+        case 0: return pick_d0(both, track, alpha1);
+        case 1: return pick_d1(both, track, alpha1);
+        case 2: return pick_d2(both, track, alpha1);
+        default: return pick_d3(both, track, alpha1);
+    }
+}
+
+uint32_t half2_bits(float v) {
+    const __half2 h = __floats2half2_rn(v, v);
+    uint32_t u;
+    std::memcpy(&u, &h, 4);
+    return u;
+}
+
+struct Layout {
+    int32_t W, WP, G, Tb;
+    int32_t part_w[5];
+    int32_t smem_A, smem_B, smem_slot, smem_h, smem_e, smem_bar, total;
+};
+
+bool plan(const TcImage &img, const AnnealArgs &a, Layout *L, std::string *why) {
+    if (!img.ok) {
+        *why = img.why;
+        return false;
+    }
+    if (a.N != int32_t(img.h_unit.size())) {
+        *why = "instance mismatch";
+        return false;
+    }
+    if (a.R > kCT) {
+        *why = "R > 128";
+        return false;
+    }
+    if (img.nh > kMaxNh) {
+        *why = "too many h digit columns";
+        return false;
+    }
+    const int64_t jpmax = std::max<int64_t>(std::llabs(int64_t(a.jperp_min)),
+                                            std::llabs(int64_t(a.jperp_min) + int64_t(a.jperp_step) * a.beta));
+    if (int64_t(a.I0) + a.n_rnd + (a.both ? 2 : 1) * jpmax > 1024) {
+        *why = "I0 + n_rnd + |J_perp| terms exceed the exact FP16 epilogue range (1024)";
+        return false;
+    }
+    L->W = (a.N + 31) / 32;
+    L->WP = L->W | 1;
+    L->G = (a.N + 15) / 16;
+    L->Tb = kCT / a.R;
+    for (int q = 0; q <= 4; ++q) L->part_w[q] = q * L->W / 4;
+    for (int q = 0; q < 4; ++q) {
+        const int nw = L->part_w[q + 1] - L->part_w[q];
+        const int ng = std::min(2 * L->part_w[q + 1], L->G) - 2 * L->part_w[q];
+        if (nw > kMaxW || ng > kMaxG) {
+            *why = "N too large for the resident epilogue split";
+            return false;
+        }
+    }
+    int32_t off = 0;
+    L->smem_A = off;
+    off += kCT * img.Kp;
+    L->smem_B = off;
+    off += img.Brows * img.Kp;
+    L->smem_slot = off;
+    off += (kCT * L->WP * 4 + 15) / 16 * 16;
+    L->smem_h = off;
+    off += (a.N * 4 + 15) / 16 * 16;
+    L->smem_e = off;
+    off += kCT * 8;
+    L->smem_bar = off;
+    off += 64;
+    L->total = off + 1024;  // alignment slack
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (optin <= 0) optin = 232448;
+    if (L->total > optin) {
+        *why = "operands do not fit in shared memory (" + std::to_string(L->total) + " bytes)";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+bool tc_supported(const TcImage &img, const AnnealArgs &a, std::string *why) {
+    Layout L;
+    return plan(img, a, &L, why);
+}
+
+int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream) {
+    Layout L;
+    std::string why;
+    if (!plan(img, a, &L, &why)) return fail(SSQA_ERR_UNSUPPORTED, "tensor path: " + why);
+    TcParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.a = a;
+    p.b_img = dc.tc_b;
+    p.h_unit = dc.tc_h_unit;
+    p.Kp = img.Kp;
+    p.N16 = img.N16;
+    p.nh = img.nh;
+    p.nchunk = img.nchunk;
+    p.Brows = img.Brows;
+    p.jm = img.jm;
+    p.Tb = L.Tb;
+    p.W = L.W;
+    p.WP = L.WP;
+    p.G = L.G;
+    p.crow[0] = img.chunk_rows[0];
+    p.crow[1] = img.chunk_rows[1];
+    for (int q = 0; q <= 4; ++q) p.part_w[q] = L.part_w[q];
+    for (int ch = 0; ch < 2; ++ch) {
+        // instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B
+        // E4M3 (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+        p.idesc[ch] = (1u << 4) | (uint32_t(img.chunk_rows[ch] >> 3) << 17) | (uint32_t(kCT >> 4) << 24);
+    }
+    uint32_t tc = 32;
+    while (tc < uint32_t(img.Brows)) tc <<= 1;
+    p.tmem_cols = tc;
+    for (int m = 0; m < img.nh; ++m) p.a_w[m] = img.a_w[m];
+    p.JM2 = half2_bits(float(img.jm));
+    p.NR2 = half2_bits(float(a.n_rnd));
+    p.I02 = half2_bits(float(a.I0));
+    p.NI02 = half2_bits(-float(a.I0));
+    p.I0MA2 = half2_bits(float(a.I0 - a.alpha));
+    p.smem_A = L.smem_A;
+    p.smem_B = L.smem_B;
+    p.smem_slot = L.smem_slot;
+    p.smem_h = L.smem_h;
+    p.smem_e = L.smem_e;
+    p.smem_bar = L.smem_bar;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *err = nullptr;
+    cudaError_t e = cudaMallocAsync(&err, sizeof(int), st);
+    if (e) return fail(SSQA_ERR_OOM, std::string("tensor path: ") + cudaGetErrorString(e));
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    p.err = err;
+    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, a.alpha == 1);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    const int64_t grid = (int64_t(a.trials) + L.Tb - 1) / L.Tb;
+    fn<<<unsigned(grid), kThreads, L.total, st>>>(p);
+    e = cudaGetLastError();
+    int herr = 0;
+    if (!e) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(err, st);
+    if (e) return fail(SSQA_ERR_DEVICE, std::string("tensor path kernel: ") + cudaGetErrorString(e));
+    if (herr) return fail(SSQA_ERR_TIMEOUT, "tensor path: a bounded wait for the tensor cores timed out");
+    return SSQA_OK;
+}
+
+}  // namespace ssqa

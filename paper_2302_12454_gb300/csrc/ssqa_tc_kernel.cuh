@@ -1,0 +1,559 @@
+// Persistent tensor-core kernel of SSQA for sm_103a (tcgen05 + TMEM).
+//
+// One CTA owns 128 spin columns c = (trial, replica k) -- whole trials, so
+// the replica ring of Eq. 4 / Fig. 2 stays inside the CTA -- and runs every
+// annealing cycle of Eq. 6a-6c for them in one launch, with no global-memory
+// traffic inside the cycle loop:
+//
+//   shared memory  A = sigma(t) as FP8 E4M3 (+1/-1), 128 x Kp, rewritten each
+//                  cycle by the epilogue; B = J / jm and the h digits, read
+//                  once from global memory; one word-per-32-spins bit slot
+//                  with sigma(t - d) of every column for the replica term.
+//   tensor memory  D[c][i] = sum_j sigma_{j,c}(t) J_ij / jm + h_i / jm, FP32,
+//                  produced by tcgen05.mma kind::f8f6f4 (exact: every operand
+//                  is a small integer and every partial sum is below 2^14).
+//   registers      the integral counters Is (Eq. 6b) as packed half2, and the
+//                  thread's own spin history as bit words.
+//
+// Warp roles: all 16 warps run the epilogue (warp w reads TMEM lanes
+// 32*(w%4).., i.e. columns, and a quarter (w/4) of the spins); warp 0 also
+// allocates TMEM and its lane 0 issues the MMAs.  Per cycle:
+//   MMA(sigma(t)) -> commit -> epilogue: D -> local field (Eq. 6a) ->
+//   counter (Eq. 6b) -> sign (Eq. 6c) -> sigma(t+1) into A -> barrier.
+// Epilogue arithmetic is exact in FP16: the local field is an integer, and
+// any value above 2048 in magnitude (the only ones FP16 rounds) saturates
+// the counter in the same direction as the exact value, because the host
+// limits I0 + n_rnd + |J_perp| terms to 1024.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <cstring>
+
+#include "philox.cuh"
+#include "ssqa_internal.h"
+
+namespace ssqa {
+namespace tc {
+
+constexpr int kCT = 128;                 // spin columns per CTA (MMA M)
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = kEpiWarps * 32;
+constexpr int kMaxG = 7;                 // 16-spin granules per epilogue thread
+constexpr int kMaxW = 4;                 // 32-spin words per epilogue thread
+constexpr uint32_t kSignPair = 0x80008000u;
+constexpr int kMaxNh = 16;
+constexpr long long kWaitNs = 4000000000LL;  // bounded waits: 4 s
+
+struct TcParams {
+    AnnealArgs a;
+    const uint8_t *b_img;
+    const int32_t *h_unit;
+    int32_t Kp, N16, nh, nchunk, Brows, jm, Tb, W, WP, G;
+    int32_t crow[2];
+    int32_t part_w[5];
+    uint32_t idesc[2];
+    uint32_t tmem_cols;
+    uint8_t a_w[kMaxNh];
+    uint32_t JM2, NR2, I02, NI02, I0MA2;
+    int32_t smem_A, smem_B, smem_slot, smem_h, smem_e, smem_bar;
+    int *err;
+};
+
+// ----------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of an mbarrier; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// D(tmem) (+)= A(smem) * B(smem)^T, FP8 operands, FP32 accumulate.
+__device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit TMEM columns; waits for completion.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])::"memory");
+}
+// Shared-memory matrix descriptor (tcgen05), no swizzle, K-major:
+// core matrices of 8 rows x 16 bytes; LBO = stride between K-adjacent core
+// matrices, SBO = stride between 8-row groups; version field = 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t((lbo & 0x3FFFFu) >> 4) << 16) |
+           (uint64_t((sbo & 0x3FFFFu) >> 4) << 32) | (uint64_t(1) << 46);
+}
+
+// ------------------------------------------------------------- half2 helpers
+__device__ __forceinline__ uint32_t h2u(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+__device__ __forceinline__ __half2 u2h(uint32_t u) {
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+// FP32 pair (lo, hi) -> packed half2 (round to nearest; exact for |x| <= 2048)
+__device__ __forceinline__ uint32_t pack_h2(uint32_t lo_bits, uint32_t hi_bits) {
+    return h2u(__floats2half2_rn(__uint_as_float(lo_bits), __uint_as_float(hi_bits)));
+}
+// Element offset of (row r, k) in the core-matrix layout.
+__device__ __forceinline__ uint32_t cm_off(int r, int k, int Kp) {
+    return uint32_t((r >> 3) * (Kp * 8) + (k >> 4) * 128 + (r & 7) * 16 + (k & 15));
+}
+// Four sign-carrying half2 words (bits 15/31) -> 16 FP8 E4M3 bytes +1/-1.
+__device__ __forceinline__ uint4 fp8_bytes(const uint32_t (&s)[8]) {
+    uint4 o;
+    o.x = (__byte_perm(s[0], s[1], 0x7531) & 0x80808080u) | 0x38383838u;
+    o.y = (__byte_perm(s[2], s[3], 0x7531) & 0x80808080u) | 0x38383838u;
+    o.z = (__byte_perm(s[4], s[5], 0x7531) & 0x80808080u) | 0x38383838u;
+    o.w = (__byte_perm(s[6], s[7], 0x7531) & 0x80808080u) | 0x38383838u;
+    return o;
+}
+
+// Keep only the bytes of spins < N in a 16-byte granule starting at spin i0.
+__device__ __forceinline__ uint4 mask_tail(uint4 b, int i0, int N) {
+    auto m = [&](int q) -> uint32_t {
+        const int nv = N - (i0 + 4 * q);
+        return nv >= 4 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : ((1u << (8 * nv)) - 1u));
+    };
+    b.x &= m(0);
+    b.y &= m(1);
+    b.z &= m(2);
+    b.w &= m(3);
+    return b;
+}
+
+// Sign bit (set = -1) of spin i inside a 32-spin word with the pair layout.
+__device__ __forceinline__ uint32_t word_bit(uint32_t w, uint32_t i) { return (w >> spin_bit_pos(i)) & 1u; }
+
+// ------------------------------------------------------------------- kernel
+template <int D, bool kBoth, bool kTrack, bool kAlpha1>
+__global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_constant__ TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = sm + p.smem_A;
+    uint8_t *sB = sm + p.smem_B;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + p.smem_slot);
+    float *sh = reinterpret_cast<float *>(sm + p.smem_h);
+    unsigned long long *eacc = reinterpret_cast<unsigned long long *>(sm + p.smem_e);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + p.smem_bar);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3);
+
+    const AnnealArgs &a = p.a;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool mma_warp = warp == 0;  // allocates TMEM; lane 0 issues the MMAs
+    const int Kp = p.Kp;
+    const int64_t trial0 = int64_t(blockIdx.x) * p.Tb;
+    const int ntr = int(a.trials - trial0 < p.Tb ? a.trials - trial0 : p.Tb);
+    const int vcols = ntr * a.R;
+    const int64_t col0 = trial0 * a.R;  // global column of local column 0
+    const bool need_final = a.e_final != nullptr || kTrack;
+    const int iters = a.cycles + (need_final ? 1 : 0);
+
+    // ---------------------------------------------------------------- set-up
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (mma_warp) {
+        tmem_alloc(tmem_holder, p.tmem_cols);
+        tmem_relinquish();
+    }
+    {
+        uint4 *A4 = reinterpret_cast<uint4 *>(sA);
+        for (int x = tid; x < kCT * Kp / 16; x += kThreads) A4[x] = make_uint4(0, 0, 0, 0);
+        const uint4 *g4 = reinterpret_cast<const uint4 *>(p.b_img);
+        uint4 *B4 = reinterpret_cast<uint4 *>(sB);
+        for (int x = tid; x < p.Brows * Kp / 16; x += kThreads) B4[x] = __ldg(&g4[x]);
+        for (int x = tid; x < a.N; x += kThreads) sh[x] = float(__ldg(&p.h_unit[x]));
+        for (int x = tid; x < kCT; x += kThreads) eacc[x] = 0ull;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    for (int x = tid; x < vcols * p.nh; x += kThreads) {
+        const int c = x / p.nh, m = x % p.nh;
+        sA[cm_off(c, p.N16 + m, Kp)] = p.a_w[m];
+    }
+    const uint32_t tmem = *tmem_holder;
+
+    // epilogue thread identity
+    const int qd = warp & 3, part = warp >> 2;
+    const int c = qd * 32 + lane;                      // local column = TMEM lane
+    const bool valid = c < vcols;
+    const int lt = valid ? c / a.R : 0, k = valid ? c % a.R : 0;
+    const uint32_t trial_g = a.trial_offset + uint32_t(trial0 + lt);
+    const int nb_up = lt * a.R + (k + 1) % a.R;
+    const int nb_dn = lt * a.R + (k + a.R - 1) % a.R;
+    const int w0 = p.part_w[part];
+    const int w1 = p.part_w[part + 1];
+    const int g0 = 2 * w0;
+    const int ng = min(2 * w1, p.G) - g0;
+    const uint32_t key0 = uint32_t(a.seed), key1 = uint32_t(a.seed >> 32);
+
+    uint32_t Is2[kMaxG][8];
+    uint32_t H[D + 1][kMaxW];
+#pragma unroll
+    for (int g = 0; g < kMaxG; ++g)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Is2[g][q] = 0u;
+#pragma unroll
+    for (int l = 0; l <= D; ++l)
+#pragma unroll
+        for (int q = 0; q < kMaxW; ++q) H[l][q] = 0u;
+    int64_t e_best = LLONG_MAX;
+    int32_t best_cycle = -1;
+    int64_t e_fin = 0;
+
+    // --------------------------------------------- initial state sigma(t0)
+    if (valid) {
+        const int64_t gcol = col0 + c;
+        const int64_t ht = trial0 + lt;
+#pragma unroll
+        for (int g = 0; g < kMaxG; ++g) {
+            if (g >= ng) continue;
+            const int i0 = (g0 + g) * 16;
+            const int half = (g0 + g) & 1;
+            const int lw = g >> 1;  // g0 is even
+            uint32_t s[8];
+            if (a.init_mode == SSQA_INIT_FROM_STATE) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = i0 + 2 * q;
+                    const uint32_t lo = (i < a.N && a.sigma[gcol * a.N + i] < 0) ? 0x8000u : 0u;
+                    const uint32_t hi = (i + 1 < a.N && a.sigma[gcol * a.N + i + 1] < 0) ? 0x80000000u : 0u;
+                    s[q] = lo | hi;
+                    const int32_t v0 = i < a.N ? a.Is[gcol * a.N + i] : 0;
+                    const int32_t v1 = i + 1 < a.N ? a.Is[gcol * a.N + i + 1] : 0;
+                    Is2[g][q] = h2u(__floats2half2_rn(float(v0), float(v1)));
+                }
+            } else {
+                uint32_t w = 0xFFFFFFFFu;  // all -1
+                if (a.init_mode == SSQA_INIT_RANDOM)
+                    w = noise_word(a.seed, uint32_t(i0), uint32_t(k), trial_g, 0xFFFFFFFFu);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s[q] = (w << (half * 8 + q)) & kSignPair;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) H[0][lw] |= s[q] >> (half * 8 + q);
+            uint4 b = fp8_bytes(s);
+            if (i0 + 16 > a.N) b = mask_tail(b, i0, a.N);  // spins beyond N stay 0 in A
+            *reinterpret_cast<uint4 *>(sA + cm_off(c, i0, Kp)) = b;
+        }
+        // older levels sigma(t0 - l)
+#pragma unroll
+        for (int l = 1; l <= D; ++l) {
+#pragma unroll
+            for (int q = 0; q < kMaxW; ++q) {
+                if (2 * q >= ng) continue;
+                if (a.init_mode == SSQA_INIT_FROM_STATE) {
+                    uint32_t w = 0;
+                    for (int e = 0; e < 32; ++e) {
+                        const int i = (w0 + q) * 32 + e;
+                        if (i < a.N && a.hist[((ht * D + (l - 1)) * a.R + k) * int64_t(a.N) + i] < 0)
+                            w |= 1u << spin_bit_pos(uint32_t(i));
+                    }
+                    H[l][q] = w;
+                } else {
+                    H[l][q] = H[0][q];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxW; ++q)
+            if (2 * q < ng) slot[c * p.WP + w0 + q] = H[D][q];
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    bar_sync(1, kThreads);
+
+    // ------------------------------------------------------------ cycle loop
+    const int64_t period = int64_t(a.tau) * (a.beta + 1);
+    for (int it = 0; it < iters; ++it) {
+        const int64_t t = int64_t(a.start_cycle) + it;
+        const bool update = it < a.cycles;
+        const bool energy = (kTrack && it > 0) || !update;
+        const uint32_t parity = uint32_t(it) & 1u;
+        if (*abort_flag) break;
+        if (mma_warp) {
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t a_base = smem_u32(sA);
+                const uint32_t b_base = smem_u32(sB);
+                int row0 = 0;
+                for (int ch = 0; ch < p.nchunk; ++ch) {
+                    const uint32_t d_tmem = tmem + uint32_t(row0);
+                    for (int s = 0; s < Kp / 32; ++s) {
+                        const uint64_t ad = smem_desc(a_base + uint32_t(s) * 256u, 128u, uint32_t(Kp) * 8u);
+                        const uint64_t bd = smem_desc(b_base + uint32_t(row0 / 8) * uint32_t(Kp) * 8u +
+                                                          uint32_t(s) * 256u,
+                                                      128u, uint32_t(Kp) * 8u);
+                        mma_f8f6f4(d_tmem, ad, bd, p.idesc[ch], s > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&bars[ch]);
+                    row0 += p.crow[ch];
+                }
+            }
+            __syncwarp();
+        }
+        {
+            const int64_t lvl = (t % period) / a.tau;
+            const float jpf = float(int64_t(a.jperp_min) + lvl * a.jperp_step);
+            const uint32_t JP2 = h2u(__floats2half2_rn(jpf, jpf));
+            bool waited0 = false, waited1 = false;
+            int cur_blk = -1;
+            Philox4 ph;
+            ph.x[0] = ph.x[1] = ph.x[2] = ph.x[3] = 0;
+            uint32_t newW[kMaxW];
+#pragma unroll
+            for (int q = 0; q < kMaxW; ++q) newW[q] = 0u;
+            float esum = 0.f;
+            uint32_t up_w = 0, dn_w = 0;
+#pragma unroll
+            for (int g = 0; g < kMaxG; ++g) {
+                if (g >= ng) continue;
+                const int gg = g0 + g;
+                const int i0 = gg * 16;
+                const int half = gg & 1;
+                const int lw = g >> 1;
+                const int ch = (p.nchunk > 1 && i0 >= p.crow[0]) ? 1 : 0;
+                if (ch == 0 && !waited0) {
+                    if (!mbar_wait(&bars[0], parity)) {
+                        *abort_flag = 1;
+                        atomicExch(p.err, 1);
+                    }
+                    waited0 = true;
+                    tc_fence_after();
+                }
+                if (ch == 1 && !waited1) {
+                    if (!mbar_wait(&bars[1], parity)) {
+                        *abort_flag = 1;
+                        atomicExch(p.err, 1);
+                    }
+                    waited1 = true;
+                    tc_fence_after();
+                }
+                uint32_t f[16];
+                tmem_ld16(tmem + (uint32_t(qd * 32) << 16) + uint32_t(i0), f);
+                if (!valid) continue;
+                if (kTrack || !update) {
+                    if (energy) {
+                        // E' = -(jm/2) sum_i sigma_i(t) (D_i + h_i/jm): sigma(t) is H[0]
+                        const uint32_t sw = H[0][lw];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int j = half * 8 + q;
+                            const int i = i0 + 2 * q;
+                            const float y0 = __uint_as_float(f[2 * q]) + (i < a.N ? sh[i] : 0.f);
+                            const float y1 = __uint_as_float(f[2 * q + 1]) + (i + 1 < a.N ? sh[i + 1] : 0.f);
+                            const uint32_t sl = (sw << (16 + j)) & 0x80000000u;
+                            const uint32_t shi = (sw << j) & 0x80000000u;
+                            esum += __uint_as_float(__float_as_uint(y0) ^ sl);
+                            esum += __uint_as_float(__float_as_uint(y1) ^ shi);
+                        }
+                    }
+                    if (!update) continue;
+                }
+                if (half == 0 || g == 0) {
+                    up_w = slot[nb_up * p.WP + (gg >> 1)];
+                    if (kBoth) dn_w = slot[nb_dn * p.WP + (gg >> 1)];
+                }
+                const int blk = i0 >> 7;
+                if (blk != cur_blk) {
+                    ph = philox4x32_10(uint32_t(blk), uint32_t(k), trial_g, uint32_t(t), key0, key1);
+                    cur_blk = blk;
+                }
+                const int wsel = (i0 >> 5) & 3;
+                const uint32_t nw = wsel == 0 ? ph.x[0] : (wsel == 1 ? ph.x[1] : (wsel == 2 ? ph.x[2] : ph.x[3]));
+                uint32_t sgn[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = half * 8 + q;
+                    // Eq. 6a: jm*D = J sigma + h; +- n_rnd (noise); +- J_perp sigma_{k+1}(t - d)
+                    const uint32_t x2 = pack_h2(f[2 * q], f[2 * q + 1]);
+                    const uint32_t n2 = ((nw << j) & kSignPair) ^ p.NR2;
+                    const uint32_t c2 = ((up_w << j) & kSignPair) ^ JP2;
+                    __half2 y = __hfma2(u2h(x2), u2h(p.JM2), u2h(n2));
+                    y = __hadd2(y, u2h(c2));
+                    if (kBoth) y = __hadd2(y, u2h(((dn_w << j) & kSignPair) ^ JP2));
+                    // Eq. 6b: v = Is + I; >= I0 -> I0 - alpha; < -I0 -> -I0
+                    const __half2 v = __hadd2(u2h(Is2[g][q]), y);
+                    const __half2 m = __hmax2(v, u2h(p.NI02));
+                    uint32_t isn;
+                    if (kAlpha1) {
+                        isn = h2u(__hmin2(m, u2h(p.I0MA2)));
+                    } else {
+                        const uint32_t ge = __hge2_mask(v, u2h(p.I02));
+                        isn = (ge & p.I0MA2) | (~ge & h2u(m));
+                    }
+                    Is2[g][q] = isn;
+                    // Eq. 6c: sigma = +1 iff Is >= 0 (sign bit clear; Is is never -0)
+                    sgn[q] = isn & kSignPair;
+                    newW[lw] |= sgn[q] >> j;
+                }
+                uint4 b = fp8_bytes(sgn);
+                if (i0 + 16 > a.N) b = mask_tail(b, i0, a.N);
+                *reinterpret_cast<uint4 *>(sA + cm_off(c, i0, Kp)) = b;
+            }
+            if (energy && valid && ng > 0) atomicAdd(&eacc[c], static_cast<unsigned long long>(
+                                                                      static_cast<long long>(esum)));
+            tc_fence_before();
+            bar_sync(2, kThreads);
+            // all reads of the slot and all energy partials are done
+            if (valid) {
+                if (update) {
+#pragma unroll
+                    for (int l = D; l >= 1; --l)
+#pragma unroll
+                        for (int q = 0; q < kMaxW; ++q) H[l][q] = H[l - 1][q];
+#pragma unroll
+                    for (int q = 0; q < kMaxW; ++q) H[0][q] = newW[q];
+#pragma unroll
+                    for (int q = 0; q < kMaxW; ++q)
+                        if (2 * q < ng) slot[c * p.WP + w0 + q] = H[D][q];
+                }
+                if (energy && part == 0) {
+                    const long long s = static_cast<long long>(eacc[c]);
+                    eacc[c] = 0ull;
+                    const int64_t E = -(int64_t(p.jm) * s) / 2;
+                    if (kTrack && E < e_best) {
+                        e_best = E;
+                        best_cycle = int32_t(t);
+                    }
+                    if (!update) e_fin = E;
+                }
+            }
+            fence_proxy_async();
+        }
+        bar_sync(1, kThreads);
+    }
+
+    // ---------------------------------------------------------------- outputs
+    if (valid && !*abort_flag) {
+        const int64_t gcol = col0 + c;
+        const int64_t ht = trial0 + lt;
+#pragma unroll
+        for (int g = 0; g < kMaxG; ++g) {
+            if (g >= ng) continue;
+            const int i0 = (g0 + g) * 16;
+            const int lw = g >> 1;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 v = __half22float2(u2h(Is2[g][q]));
+                const int i = i0 + 2 * q;
+                if (i < a.N) a.Is[gcol * a.N + i] = int32_t(v.x);
+                if (i + 1 < a.N) a.Is[gcol * a.N + i + 1] = int32_t(v.y);
+            }
+            for (int e = 0; e < 16; ++e) {
+                const int i = i0 + e;
+                if (i >= a.N) break;
+                a.sigma[gcol * a.N + i] = word_bit(H[0][lw], uint32_t(i)) ? int8_t(-1) : int8_t(1);
+                if (a.hist)
+#pragma unroll
+                    for (int l = 0; l < D; ++l)
+                        a.hist[((ht * D + l) * a.R + k) * int64_t(a.N) + i] =
+                            word_bit(H[l + 1][lw], uint32_t(i)) ? int8_t(-1) : int8_t(1);
+            }
+        }
+        if (part == 0) {
+            if (a.e_final) a.e_final[gcol] = e_fin;
+            if (kTrack) {
+                a.e_best[gcol] = e_best;
+                a.best_cycle[gcol] = best_cycle;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (mma_warp) {
+        tc_fence_after();
+        tmem_dealloc(tmem, p.tmem_cols);
+    }
+}
+
+using KernelFn = void (*)(TcParams);
+
+// Kernel variants are split over several translation units (one per delay d)
+// so that they compile in parallel.
+KernelFn pick_d0(bool both, bool track, bool alpha1);
+KernelFn pick_d1(bool both, bool track, bool alpha1);
+KernelFn pick_d2(bool both, bool track, bool alpha1);
+KernelFn pick_d3(bool both, bool track, bool alpha1);
+
+#define SSQA_TC_DEFINE_PICK(DD)                                                                        \
+    KernelFn pick_d##DD(bool both, bool track, bool alpha1) {                                           \
+        if (DD == 1 && !both && !track && alpha1) return ssqa_tc_kernel<DD, false, false, (DD == 1)>;  \
+        if (both) return track ? ssqa_tc_kernel<DD, true, true, false> : ssqa_tc_kernel<DD, true, false, false>; \
+        return track ? ssqa_tc_kernel<DD, false, true, false> : ssqa_tc_kernel<DD, false, false, false>;  \
+    }
+
+}  // namespace tc
+}  // namespace ssqa
