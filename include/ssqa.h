@@ -196,6 +196,32 @@ typedef struct ssqa_result {
 int ssqa_anneal(const ssqa_ising *ising, const ssqa_params *params, ssqa_result *out,
                 void *cuda_stream);
 
+/* ssqa_anneal_noalloc -- the plain CUDA-core anneal (the computation of
+ * ssqa_anneal with SSQA_ALGO_PLAIN) without any device-memory allocation.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate device memory: code running while a stream is captured
+ * into a CUDA graph, plugins or real-time loops whose host framework owns
+ * all device memory and forbids cudaMalloc after start-up, and deployments
+ * that fix their device footprint at initialisation.
+ *   N: spins; J_padded: device, N rows of roundup(N, 16) bytes (row pitch
+ *   roundup(N, 16), zero padded), symmetric J' with zero diagonal; h: device,
+ *   N int32.  params: as for ssqa_anneal; flags must include
+ *   SSQA_FLAG_DEVICE_PTRS (all `out` pointers are device pointers); algo is
+ *   ignored.  The call only enqueues work on cuda_stream.
+ * Scratch: one fixed 16 MiB device array inside the library, held on every
+ * GPU that loads the library until the process exits.  A problem needing
+ * (delay + 2) * trials * R * roundup(N, 16) bytes plus 16 bytes per column
+ * (and alignment) beyond that returns SSQA_ERR_INVALID_ARG.  Every call
+ * shares the array and re-initialises what it reads, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads on the
+ * same device) race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address (once
+ * per device); make that first call before any stream capture begins.
+ * Never calls cudaMalloc, cudaFree or any allocating routine.
+ * Errors: SSQA_ERR_INVALID_ARG, SSQA_ERR_DEVICE. */
+int ssqa_anneal_noalloc(int32_t N, const int8_t *J_padded, const int32_t *h, const ssqa_params *params,
+                        ssqa_result *out, void *cuda_stream);
+
 /* Problem energy E'(sigma) = -sum_i h'_i s_i - sum_{i<j} J'_ij s_i s_j
  * (Eq. 1; Eq. 5 per replica) of `count` spin vectors, on the GPU.
  *   sigma: count*N int8 (+1/-1); E_out: count int64.

@@ -69,6 +69,7 @@ def lib():
         L.ssqa_params_default.restype = None
         L.ssqa_anneal.argtypes = [vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
         L.ssqa_energy.argtypes = [vp, vp, i64, vp, u32, vp]
+        L.ssqa_anneal_noalloc.argtypes = [i32, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
         L.ssqa_tts.argtypes = [ctypes.c_double] * 3
         L.ssqa_tts.restype = ctypes.c_double
         L.ssqa_last_error.argtypes = []
