@@ -25,10 +25,13 @@
  *     (h' = S h, J' = S J, I0' = S I0, n_rnd' = S n_rnd, J_perp' = S J_perp,
  *     alpha' = 1 LSB); with S = 12 every value of Table 2 is an integer;
  *   - the noise r_{i,k}(t) in {-1,+1} is drawn per (spin, replica, trial,
- *     cycle) from Philox4x32-10 (Salmon et al., SC'11): counter
- *     (i / 128, k, trial, t), key (seed low word, seed high word); spin i
- *     takes word (i % 128) / 32 and, inside that word, bit 15 - e/2 for even
- *     e = i % 32 and bit 31 - (e-1)/2 for odd e; a set bit means r = -1;
+ *     cycle) from Philox4x32-10 (Salmon et al., SC'11).  Spins are grouped
+ *     in 32-spin words w = i / 32; word w takes output word (w / 4) % 4 of
+ *     the Philox call with counter (4 (w / 16) + w % 4, k, trial, t) and key
+ *     (seed low word, seed high word), so one call serves words
+ *     {16 j + q, 16 j + q + 4, 16 j + q + 8, 16 j + q + 12}; inside its word,
+ *     spin i takes bit 15 - e/2 for even e = i % 32 and bit 31 - (e-1)/2 for
+ *     odd e; a set bit means r = -1;
  *   - sigma(0) uses the same bit with t = 0xFFFFFFFF (set bit: sigma = -1),
  *     Is(0) = 0, and sigma(t - d) = sigma(0) for t < d;
  *   - random graphs come from SplitMix64 (Steele, Lea, Flood, OOPSLA'14).
@@ -306,11 +309,12 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 /* The random bit of spin i, replica k, trial, cycle t (reading in header). */
 int or_noise_bit(uint64_t seed, uint32_t i, uint32_t k, uint32_t trial, uint32_t t)
 {
-    uint32_t ctr[4], key[2], out[4], w, e, b;
-    ctr[0] = i / 128u; ctr[1] = k; ctr[2] = trial; ctr[3] = t;
+    uint32_t ctr[4], key[2], out[4], w, word, e, b;
+    word = i / 32u;
+    ctr[0] = 4u * (word / 16u) + word % 4u; ctr[1] = k; ctr[2] = trial; ctr[3] = t;
     key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
     or_philox4x32_10(ctr, key, out);
-    w = out[(i % 128u) / 32u];
+    w = out[(word / 4u) % 4u];
     e = i % 32u;
     b = (e & 1u) ? (31u - (e >> 1)) : (15u - (e >> 1));
     return (int)((w >> b) & 1u);

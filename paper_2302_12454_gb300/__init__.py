@@ -239,3 +239,56 @@ def energy(ising: Ising, sigma) -> np.ndarray:
 
 def tts(t: float, p_s: float, p_target: float = 0.99) -> float:
     return float(lib().ssqa_tts(t, p_s, p_target))
+
+
+# ----------------------------------------------------------------- serving
+class Server:
+    """Continuous-batching server (ssqa_server_*): submit anneals, poll results."""
+
+    def __init__(self, hbm_budget: int, max_slots: int = 4, device: int = 0):
+        self._s = ctypes.c_void_p()
+        _check(lib().ssqa_server_create(hbm_budget, max_slots, device, ctypes.byref(self._s)), "server_create")
+        self._pending = {}
+
+    def submit(self, ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_best: bool = False,
+               **kw) -> int:
+        p = make_params(R=R, cycles=cycles, trials=trials, seed=seed, **kw)
+        if track_best:
+            p.flags |= FLAG_TRACK_BEST
+        t = ctypes.c_uint64()
+        _check(lib().ssqa_submit(self._s, ising.handle, ctypes.byref(p), ctypes.byref(t)), "submit")
+        self._pending[t.value] = (ising, p)  # keeps the instance alive until polled
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """Returns None while pending, else (result dict, latency in seconds)."""
+        ising, p = self._pending[ticket]
+        N, T, R, d = ising.N, p.trials, p.R, p.delay
+        out = dict(sigma=np.zeros((T, R, N), np.int8), Is=np.zeros((T, R, N), np.int32),
+                   E_final=np.zeros((T, R), np.int64))
+        if d:
+            out["hist"] = np.zeros((T, d, R, N), np.int8)
+        tb = p.flags & FLAG_TRACK_BEST
+        if tb:
+            out["E_best"] = np.zeros((T, R), np.int64)
+            out["best_cycle"] = np.zeros((T, R), np.int32)
+        r = Result(_ptr(out["sigma"]), _ptr(out.get("hist")), _ptr(out["Is"]), _ptr(out["E_final"]),
+                   _ptr(out.get("E_best")), _ptr(out.get("best_cycle")))
+        lat = ctypes.c_double()
+        rc = lib().ssqa_poll(self._s, ticket, ctypes.byref(r), timeout_ms, ctypes.byref(lat))
+        if rc == PENDING:
+            return None
+        del self._pending[ticket]
+        _check(rc, "poll")
+        return out, lat.value * 1e-6
+
+    def close(self):
+        if self._s is not None and self._s.value:
+            lib().ssqa_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

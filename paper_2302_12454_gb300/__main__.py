@@ -1,0 +1,84 @@
+"""Command line: run SSQA anneals on a named synthetic workload.
+
+  python -m paper_2302_12454_gb300 anneal --workload batched_gi_n20 \\
+      [--cycles C] [--trials T] [--algo tensor|plain|auto] [--repeat K]
+
+Prints one line per run: device time of the anneal (CUDA events on the
+launching stream), spin-updates/s, success probability P_s (any replica at
+the ground energy -e_offset, GI workloads) and the time to solution of
+Eq. 10.  Buffers stay on the device; nothing is copied back except the
+final energies.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+import numpy as np
+
+
+def _instance(S, W, cfg):
+    if cfg["kind"] == "gi":
+        a = S.gen_er_graph(cfg["n"], W.p_q32(cfg["p"]), cfg["graph_seed"])
+        b, _ = S.permute_graph(a, cfg["perm_seed"])
+        return S.Ising.gi(a, b), True
+    N = cfg["N"]
+    return S.Ising.dense(W.sk_couplings(N, cfg["j_seed"]), np.zeros(N, np.int32)), False
+
+
+def cmd_anneal(args):
+    import torch
+
+    import paper_2302_12454_gb300 as S
+    from paper_2302_12454_gb300 import build as B
+    from paper_2302_12454_gb300 import workloads as W
+
+    B.build()
+    cfg = dict(W.CONFIGS[args.workload])
+    if args.cycles is not None:
+        cfg["cycles"] = args.cycles
+    if args.trials is not None:
+        cfg["trials"] = args.trials
+    I, has_ground = _instance(S, W, cfg)
+    h, J, off = I.export()
+    N, R, T = h.shape[0], cfg["R"], cfg["trials"]
+    algo = {"auto": S.ALGO_AUTO, "tensor": S.ALGO_TENSOR, "plain": S.ALGO_PLAIN}[args.algo]
+    p = S.make_params(R=R, cycles=cfg["cycles"], trials=T, seed=cfg["seed"], tau=cfg["tau"], algo=algo)
+    sig = torch.empty((T, R, N), dtype=torch.int8, device="cuda")
+    Is = torch.empty((T, R, N), dtype=torch.int32, device="cuda")
+    E = torch.empty((T, R), dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream()
+    for k in range(args.repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        S.anneal_device(I, p, sig, Is, e_final=E, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        rec = dict(run=k, workload=args.workload, N=N, R=R, cycles=cfg["cycles"], trials=T, algo=args.algo,
+                   seconds=t, spin_updates_per_s=N * R * T * cfg["cycles"] / t)
+        if has_ground:
+            ps = float((E.min(dim=1).values.cpu().numpy() == -off).mean())
+            rec.update(p_s=ps, tts_s=S.tts(t / T, ps, 0.99))
+        print(json.dumps(rec), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_2302_12454_gb300")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    a = sub.add_parser("anneal", help="run anneals of a named workload on cuda:0")
+    from paper_2302_12454_gb300 import workloads as W
+
+    a.add_argument("--workload", default="batched_gi_n20", choices=sorted(W.CONFIGS))
+    a.add_argument("--cycles", type=int)
+    a.add_argument("--trials", type=int)
+    a.add_argument("--algo", default="auto", choices=["auto", "tensor", "plain"])
+    a.add_argument("--repeat", type=int, default=1)
+    args = ap.parse_args(argv)
+    if args.cmd == "anneal":
+        cmd_anneal(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

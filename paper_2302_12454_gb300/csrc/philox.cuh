@@ -2,7 +2,10 @@
 // random numbers: as easy as 1, 2, 3", SC'11), device side.  The paper's
 // noise r_i(t) (Eq. 2a, Eq. 6a) is a random +-1 per spin and cycle; its
 // generator is not specified, so this library draws it from Philox keyed by
-// the anneal seed with counter (spin block i/128, replica k, trial, cycle t).
+// the anneal seed.  Spins are grouped in 32-spin words w = i / 32; word w
+// takes output word (w / 4) % 4 of the call with counter
+// (4 (w / 16) + w % 4, replica k, trial, cycle t), so one call covers the
+// four words w, w + 4, w + 8, w + 12 of a 16-word group.
 #pragma once
 #include <cstdint>
 
@@ -48,10 +51,16 @@ __device__ __forceinline__ uint32_t spin_bit_pos(uint32_t i) {
     return (e & 1u) ? (31u - (e >> 1)) : (15u - (e >> 1));
 }
 
+// Counter word of the Philox call serving 32-spin word `w`, and the output
+// word of that call it takes.
+__device__ __forceinline__ uint32_t noise_ctr(uint32_t w) { return 4u * (w >> 4) + (w & 3u); }
+__device__ __forceinline__ uint32_t noise_out(uint32_t w) { return (w >> 2) & 3u; }
+
 __device__ __forceinline__ uint32_t noise_word(uint64_t seed, uint32_t i, uint32_t k, uint32_t trial,
                                                uint32_t t) {
-    const Philox4 o = philox4x32_10(i >> 7, k, trial, t, uint32_t(seed), uint32_t(seed >> 32));
-    const uint32_t w = (i >> 5) & 3u;
+    const uint32_t wd = i >> 5;
+    const Philox4 o = philox4x32_10(noise_ctr(wd), k, trial, t, uint32_t(seed), uint32_t(seed >> 32));
+    const uint32_t w = noise_out(wd);
     return w == 0 ? o.x[0] : (w == 1 ? o.x[1] : (w == 2 ? o.x[2] : o.x[3]));
 }
 

@@ -126,9 +126,10 @@ void prepare_tc(ssqa_ising *I) {
         t.nchunk = 1;
         t.chunk_rows[0] = t.N16;
     } else if (N <= 512) {
+        // the smaller chunk first: its epilogue overlaps the larger chunk's MMAs
         t.nchunk = 2;
-        t.chunk_rows[0] = 256;
-        t.chunk_rows[1] = (N - 256 + 15) / 16 * 16;
+        t.chunk_rows[0] = t.N16 - 256;
+        t.chunk_rows[1] = 256;
     } else {
         t.why = "N > 512 needs more tensor memory than one CTA holds";
         return;

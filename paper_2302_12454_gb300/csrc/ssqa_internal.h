@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ssqa.h"
+#include "ssqa.h"
 
 namespace ssqa {
 

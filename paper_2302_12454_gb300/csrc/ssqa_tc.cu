@@ -15,12 +15,12 @@ namespace ssqa {
 namespace {
 using namespace tc;
 
-KernelFn pick(int d, bool both, bool track, bool alpha1) {
+KernelFn pick(int d, bool both, bool track, bool fast) {
     switch (d) {
-        case 0: return pick_d0(both, track, alpha1);
-        case 1: return pick_d1(both, track, alpha1);
-        case 2: return pick_d2(both, track, alpha1);
-        default: return pick_d3(both, track, alpha1);
+        case 0: return pick_d0(both, track, fast);
+        case 1: return pick_d1(both, track, fast);
+        case 2: return pick_d2(both, track, fast);
+        default: return pick_d3(both, track, fast);
     }
 }
 
@@ -33,7 +33,6 @@ uint32_t half2_bits(float v) {
 
 struct Layout {
     int32_t W, WP, G, Tb;
-    int32_t part_w[5];
     int32_t smem_A, smem_B, smem_slot, smem_h, smem_e, smem_bar, total;
 };
 
@@ -64,14 +63,9 @@ bool plan(const TcImage &img, const AnnealArgs &a, Layout *L, std::string *why) 
     L->WP = L->W | 1;
     L->G = (a.N + 15) / 16;
     L->Tb = kCT / a.R;
-    for (int q = 0; q <= 4; ++q) L->part_w[q] = q * L->W / 4;
-    for (int q = 0; q < 4; ++q) {
-        const int nw = L->part_w[q + 1] - L->part_w[q];
-        const int ng = std::min(2 * L->part_w[q + 1], L->G) - 2 * L->part_w[q];
-        if (nw > kMaxW || ng > kMaxG) {
-            *why = "N too large for the resident epilogue split";
-            return false;
-        }
+    if (L->W > 4 * kMaxW) {  // each of the 4 warps of a column owns words part + 4 q, q < kMaxW
+        *why = "N too large for the resident epilogue split";
+        return false;
     }
     int32_t off = 0;
     L->smem_A = off;
@@ -126,7 +120,6 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.G = L.G;
     p.crow[0] = img.chunk_rows[0];
     p.crow[1] = img.chunk_rows[1];
-    for (int q = 0; q <= 4; ++q) p.part_w[q] = L.part_w[q];
     for (int ch = 0; ch < 2; ++ch) {
         // instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B
         // E4M3 (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -138,9 +131,13 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     for (int m = 0; m < img.nh; ++m) p.a_w[m] = img.a_w[m];
     p.JM2 = half2_bits(float(img.jm));
     p.NR2 = half2_bits(float(a.n_rnd));
-    p.I02 = half2_bits(float(a.I0));
-    p.NI02 = half2_bits(-float(a.I0));
-    p.I0MA2 = half2_bits(float(a.I0 - a.alpha));
+    // fast variant: R divides 32, counters fit a biased byte, alpha = 1, and
+    // a fresh start (resumed counters may lie outside the byte range)
+    const bool fast = (32 % a.R == 0) && a.I0 <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
+    const float bias = fast ? 1152.f : 0.f;
+    p.LO2 = half2_bits(bias - float(a.I0));
+    p.HI2 = half2_bits(bias + float(a.I0 - a.alpha));
+    p.TOP2 = half2_bits(bias + float(a.I0));
     p.smem_A = L.smem_A;
     p.smem_B = L.smem_B;
     p.smem_slot = L.smem_slot;
@@ -154,7 +151,7 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     if (e) return fail(SSQA_ERR_OOM, std::string("tensor path: ") + cudaGetErrorString(e));
     cudaMemsetAsync(err, 0, sizeof(int), st);
     p.err = err;
-    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, a.alpha == 1);
+    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, fast);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     const int64_t grid = (int64_t(a.trials) + L.Tb - 1) / L.Tb;
     fn<<<unsigned(grid), kThreads, L.total, st>>>(p);

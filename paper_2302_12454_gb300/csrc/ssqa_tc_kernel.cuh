@@ -41,7 +41,7 @@ namespace tc {
 constexpr int kCT = 128;                 // spin columns per CTA (MMA M)
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = kEpiWarps * 32;
-constexpr int kMaxG = 7;                 // 16-spin granules per epilogue thread
+constexpr int kMaxG = 8;                 // 16-spin granules per epilogue thread
 constexpr int kMaxW = 4;                 // 32-spin words per epilogue thread
 constexpr uint32_t kSignPair = 0x80008000u;
 constexpr int kMaxNh = 16;
@@ -53,11 +53,11 @@ struct TcParams {
     const int32_t *h_unit;
     int32_t Kp, N16, nh, nchunk, Brows, jm, Tb, W, WP, G;
     int32_t crow[2];
-    int32_t part_w[5];
     uint32_t idesc[2];
     uint32_t tmem_cols;
     uint8_t a_w[kMaxNh];
-    uint32_t JM2, NR2, I02, NI02, I0MA2;
+    uint32_t JM2, NR2;
+    uint32_t LO2, HI2, TOP2;  // bias - I0, bias + I0 - alpha, bias + I0 (half2)
     int32_t smem_A, smem_B, smem_slot, smem_h, smem_e, smem_bar;
     int *err;
 };
@@ -125,14 +125,19 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-// 32 lanes x 16 consecutive 32-bit TMEM columns; waits for completion.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 32 lanes x 16 consecutive 32-bit TMEM columns, issued without waiting;
+// the registers are valid only after tmem_ld_wait on the same array.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+// Wait for every outstanding tcgen05.ld of this thread; `r` is tied to the
+// wait so that no use of it is scheduled before the data has arrived.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
                    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
@@ -192,8 +197,19 @@ __device__ __forceinline__ uint4 mask_tail(uint4 b, int i0, int N) {
 __device__ __forceinline__ uint32_t word_bit(uint32_t w, uint32_t i) { return (w >> spin_bit_pos(i)) & 1u; }
 
 // ------------------------------------------------------------------- kernel
-template <int D, bool kBoth, bool kTrack, bool kAlpha1>
+// kFast: R divides 32 (ring neighbours are lanes of the same warp, spin
+// history exchanged by shuffles), I0 <= 127 (each counter Is kept as the
+// byte Is + 128, four per register) and alpha = 1 (the counter update is a
+// clamp).  The general variant keeps the counters as half2, exchanges the
+// history through a shared-memory slot and applies Eq. 6b with a compare.
+// In both, counters are handled in FP16 with an offset `bias` (1152 in the
+// fast variant, where half(1024 + b) holds the byte b exactly, 0 otherwise).
+template <int D, bool kBoth, bool kTrack, bool kFast>
 __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_constant__ TcParams p) {
+    constexpr bool kShfl = kFast;
+    // Loading the next granule's accumulators while computing the current one
+    // measured slower (it waits for the second MMA chunk earlier), so off.
+    constexpr bool kPrefetch = false;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = sm + p.smem_A;
@@ -253,18 +269,23 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     const uint32_t trial_g = a.trial_offset + uint32_t(trial0 + lt);
     const int nb_up = lt * a.R + (k + 1) % a.R;
     const int nb_dn = lt * a.R + (k + a.R - 1) % a.R;
-    const int w0 = p.part_w[part];
-    const int w1 = p.part_w[part + 1];
-    const int g0 = 2 * w0;
-    const int ng = min(2 * w1, p.G) - g0;
+    // with R dividing 32 a trial never straddles a warp: neighbours are lanes
+    const int src_up = nb_up & 31, src_dn = nb_dn & 31;
+    // spin words owned by this thread: part + 4 q, q = 0..3 (one Philox call,
+    // counter `part`, gives all four noise words; every part has granules in
+    // the first MMA chunk).  Granule g = 2 q + h covers spins 16 (2 (part +
+    // 4 q) + h) .. +15 and exists when that start is below N.
+    auto gran_of = [&](int g) { return 2 * (part + 4 * (g >> 1)) + (g & 1); };
     const uint32_t key0 = uint32_t(a.seed), key1 = uint32_t(a.seed >> 32);
+    const uint32_t taddr_lane = tmem + (uint32_t(qd * 32) << 16);
 
-    uint32_t Is2[kMaxG][8];
-    uint32_t H[D + 1][kMaxW];
+    // counters: fast variant 4 biased bytes per word, general half2 pairs
+    uint32_t IsR[kMaxG][kFast ? 4 : 8];
+    uint32_t H[D + 1][kMaxW];  // own spin history, H[l] = sigma(t - l), bit words
 #pragma unroll
     for (int g = 0; g < kMaxG; ++g)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) Is2[g][q] = 0u;
+        for (int q = 0; q < (kFast ? 4 : 8); ++q) IsR[g][q] = kFast ? 0x80808080u : 0u;
 #pragma unroll
     for (int l = 0; l <= D; ++l)
 #pragma unroll
@@ -279,10 +300,11 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         const int64_t ht = trial0 + lt;
 #pragma unroll
         for (int g = 0; g < kMaxG; ++g) {
-            if (g >= ng) continue;
-            const int i0 = (g0 + g) * 16;
-            const int half = (g0 + g) & 1;
-            const int lw = g >> 1;  // g0 is even
+            const int gg = gran_of(g);
+            if (gg >= p.G) continue;
+            const int i0 = gg * 16;
+            const int half = g & 1;
+            const int lw = g >> 1;
             uint32_t s[8];
             if (a.init_mode == SSQA_INIT_FROM_STATE) {
 #pragma unroll
@@ -291,9 +313,11 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     const uint32_t lo = (i < a.N && a.sigma[gcol * a.N + i] < 0) ? 0x8000u : 0u;
                     const uint32_t hi = (i + 1 < a.N && a.sigma[gcol * a.N + i + 1] < 0) ? 0x80000000u : 0u;
                     s[q] = lo | hi;
-                    const int32_t v0 = i < a.N ? a.Is[gcol * a.N + i] : 0;
-                    const int32_t v1 = i + 1 < a.N ? a.Is[gcol * a.N + i + 1] : 0;
-                    Is2[g][q] = h2u(__floats2half2_rn(float(v0), float(v1)));
+                    if (!kFast) {
+                        const int32_t v0 = i < a.N ? a.Is[gcol * a.N + i] : 0;
+                        const int32_t v1 = i + 1 < a.N ? a.Is[gcol * a.N + i + 1] : 0;
+                        IsR[g][q] = h2u(__floats2half2_rn(float(v0), float(v1)));
+                    }
                 }
             } else {
                 uint32_t w = 0xFFFFFFFFu;  // all -1
@@ -313,11 +337,11 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         for (int l = 1; l <= D; ++l) {
 #pragma unroll
             for (int q = 0; q < kMaxW; ++q) {
-                if (2 * q >= ng) continue;
+                if (gran_of(2 * q) >= p.G) continue;
                 if (a.init_mode == SSQA_INIT_FROM_STATE) {
                     uint32_t w = 0;
                     for (int e = 0; e < 32; ++e) {
-                        const int i = (w0 + q) * 32 + e;
+                        const int i = (part + 4 * q) * 32 + e;
                         if (i < a.N && a.hist[((ht * D + (l - 1)) * a.R + k) * int64_t(a.N) + i] < 0)
                             w |= 1u << spin_bit_pos(uint32_t(i));
                     }
@@ -327,16 +351,31 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 }
             }
         }
+        if (!kShfl)
 #pragma unroll
-        for (int q = 0; q < kMaxW; ++q)
-            if (2 * q < ng) slot[c * p.WP + w0 + q] = H[D][q];
+            for (int q = 0; q < kMaxW; ++q)
+                if (gran_of(2 * q) < p.G) slot[c * p.WP + part + 4 * q] = H[D][q];
     }
     fence_proxy_async();
     tc_fence_before();
     bar_sync(1, kThreads);
 
+    // MMA descriptors: advancing one K-step (32 bytes of each row pair of
+    // core matrices = 256 bytes) adds 16 to the start-address field
+    uint64_t adesc0 = 0, bdesc0[2] = {0, 0};
+    if (mma_warp && lane == 0) {
+        adesc0 = smem_desc(smem_u32(sA), 128u, uint32_t(Kp) * 8u);
+        bdesc0[0] = smem_desc(smem_u32(sB), 128u, uint32_t(Kp) * 8u);
+        bdesc0[1] = smem_desc(smem_u32(sB) + uint32_t(p.crow[0] / 8) * uint32_t(Kp) * 8u, 128u, uint32_t(Kp) * 8u);
+    }
+    const int ksteps = Kp / 32;
+
     // ------------------------------------------------------------ cycle loop
+    // J_perp level of Table 2 tracked incrementally: sub-cycle inside a tau
+    // window, and the window index 0..beta inside one iteration
     const int64_t period = int64_t(a.tau) * (a.beta + 1);
+    int sub = int((int64_t(a.start_cycle) % period) % a.tau);
+    int lvl = int((int64_t(a.start_cycle) % period) / a.tau);
     for (int it = 0; it < iters; ++it) {
         const int64_t t = int64_t(a.start_cycle) + it;
         const bool update = it < a.cycles;
@@ -346,63 +385,74 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         if (mma_warp) {
             tc_fence_after();
             if (lane == 0) {
-                const uint32_t a_base = smem_u32(sA);
-                const uint32_t b_base = smem_u32(sB);
-                int row0 = 0;
+#pragma unroll 1
                 for (int ch = 0; ch < p.nchunk; ++ch) {
-                    const uint32_t d_tmem = tmem + uint32_t(row0);
-                    for (int s = 0; s < Kp / 32; ++s) {
-                        const uint64_t ad = smem_desc(a_base + uint32_t(s) * 256u, 128u, uint32_t(Kp) * 8u);
-                        const uint64_t bd = smem_desc(b_base + uint32_t(row0 / 8) * uint32_t(Kp) * 8u +
-                                                          uint32_t(s) * 256u,
-                                                      128u, uint32_t(Kp) * 8u);
-                        mma_f8f6f4(d_tmem, ad, bd, p.idesc[ch], s > 0 ? 1u : 0u);
-                    }
+                    const uint32_t d_tmem = tmem + uint32_t(ch ? p.crow[0] : 0);
+                    const uint32_t idesc = ch ? p.idesc[1] : p.idesc[0];
+                    const uint64_t bd0 = ch ? bdesc0[1] : bdesc0[0];
+#pragma unroll 1
+                    for (int s = 0; s < ksteps; ++s)
+                        mma_f8f6f4(d_tmem, adesc0 + uint64_t(16 * s), bd0 + uint64_t(16 * s), idesc, s > 0 ? 1u : 0u);
                     mma_commit(&bars[ch]);
-                    row0 += p.crow[ch];
                 }
             }
             __syncwarp();
         }
         {
-            const int64_t lvl = (t % period) / a.tau;
-            const float jpf = float(int64_t(a.jperp_min) + lvl * a.jperp_step);
+            const float jpf = float(a.jperp_min + lvl * a.jperp_step);
             const uint32_t JP2 = h2u(__floats2half2_rn(jpf, jpf));
             bool waited0 = false, waited1 = false;
-            int cur_blk = -1;
+            auto wait_chunk = [&](int i0) {
+                const int ch = (p.nchunk > 1 && i0 >= p.crow[0]) ? 1 : 0;
+                bool &w = ch ? waited1 : waited0;
+                if (!w) {
+                    if (!mbar_wait(&bars[ch], parity)) {
+                        *abort_flag = 1;
+                        atomicExch(p.err, 1);
+                    }
+                    w = true;
+                    tc_fence_after();
+                }
+            };
+            // noise words of this cycle: computed while the tensor cores run
             Philox4 ph;
             ph.x[0] = ph.x[1] = ph.x[2] = ph.x[3] = 0;
+            if (update && valid)
+                ph = philox4x32_10(uint32_t(part), uint32_t(k), trial_g, uint32_t(t), key0, key1);
             uint32_t newW[kMaxW];
 #pragma unroll
             for (int q = 0; q < kMaxW; ++q) newW[q] = 0u;
             float esum = 0.f;
             uint32_t up_w = 0, dn_w = 0;
+            uint32_t fb[kPrefetch ? 2 : 1][16];
+            if (kPrefetch && gran_of(0) < p.G) {
+                wait_chunk(gran_of(0) * 16);
+                tmem_ld16_issue(taddr_lane + uint32_t(gran_of(0) * 16), fb[0]);
+            }
 #pragma unroll
             for (int g = 0; g < kMaxG; ++g) {
-                if (g >= ng) continue;
-                const int gg = g0 + g;
+                const int gg = gran_of(g);
+                if (gg >= p.G) break;
+                uint32_t(&f)[16] = fb[kPrefetch ? (g & 1) : 0];
+                if (kPrefetch) {
+                    tmem_ld_wait(f);
+                    if (g + 1 < kMaxG && gran_of(g + 1) < p.G) {  // next granule loads while this one computes
+                        wait_chunk(gran_of(g + 1) * 16);
+                        tmem_ld16_issue(taddr_lane + uint32_t(gran_of(g + 1) * 16), fb[(g + 1) & 1]);
+                    }
+                } else {
+                    wait_chunk(gg * 16);
+                    tmem_ld16_issue(taddr_lane + uint32_t(gg * 16), f);
+                    tmem_ld_wait(f);
+                }
                 const int i0 = gg * 16;
-                const int half = gg & 1;
+                const int half = g & 1;
                 const int lw = g >> 1;
-                const int ch = (p.nchunk > 1 && i0 >= p.crow[0]) ? 1 : 0;
-                if (ch == 0 && !waited0) {
-                    if (!mbar_wait(&bars[0], parity)) {
-                        *abort_flag = 1;
-                        atomicExch(p.err, 1);
-                    }
-                    waited0 = true;
-                    tc_fence_after();
+                if (kShfl && update && (half == 0 || g == 0)) {
+                    // sigma(t - d) of the ring neighbours, from their lanes
+                    up_w = __shfl_sync(0xFFFFFFFFu, H[D][lw], src_up);
+                    if (kBoth) dn_w = __shfl_sync(0xFFFFFFFFu, H[D][lw], src_dn);
                 }
-                if (ch == 1 && !waited1) {
-                    if (!mbar_wait(&bars[1], parity)) {
-                        *abort_flag = 1;
-                        atomicExch(p.err, 1);
-                    }
-                    waited1 = true;
-                    tc_fence_after();
-                }
-                uint32_t f[16];
-                tmem_ld16(tmem + (uint32_t(qd * 32) << 16) + uint32_t(i0), f);
                 if (!valid) continue;
                 if (kTrack || !update) {
                     if (energy) {
@@ -422,18 +472,12 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     }
                     if (!update) continue;
                 }
-                if (half == 0 || g == 0) {
+                if (!kShfl && (half == 0 || g == 0)) {
                     up_w = slot[nb_up * p.WP + (gg >> 1)];
                     if (kBoth) dn_w = slot[nb_dn * p.WP + (gg >> 1)];
                 }
-                const int blk = i0 >> 7;
-                if (blk != cur_blk) {
-                    ph = philox4x32_10(uint32_t(blk), uint32_t(k), trial_g, uint32_t(t), key0, key1);
-                    cur_blk = blk;
-                }
-                const int wsel = (i0 >> 5) & 3;
-                const uint32_t nw = wsel == 0 ? ph.x[0] : (wsel == 1 ? ph.x[1] : (wsel == 2 ? ph.x[2] : ph.x[3]));
-                uint32_t sgn[8];
+                const uint32_t nw = ph.x[lw];
+                uint32_t isn[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int j = half * 8 + q;
@@ -444,30 +488,51 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     __half2 y = __hfma2(u2h(x2), u2h(p.JM2), u2h(n2));
                     y = __hadd2(y, u2h(c2));
                     if (kBoth) y = __hadd2(y, u2h(((dn_w << j) & kSignPair) ^ JP2));
-                    // Eq. 6b: v = Is + I; >= I0 -> I0 - alpha; < -I0 -> -I0
-                    const __half2 v = __hadd2(u2h(Is2[g][q]), y);
-                    const __half2 m = __hmax2(v, u2h(p.NI02));
-                    uint32_t isn;
-                    if (kAlpha1) {
-                        isn = h2u(__hmin2(m, u2h(p.I0MA2)));
+                    // Eq. 6b: v = Is + I; >= I0 -> I0 - alpha; < -I0 -> -I0 (offset by bias)
+                    const uint32_t ib = kFast ? __byte_perm(IsR[g][q >> 1], 0x64646464u, (q & 1) ? 0x4342 : 0x4140)
+                                              : IsR[g][q];
+                    const __half2 v = __hadd2(u2h(ib), y);
+                    const __half2 m = __hmax2(v, u2h(p.LO2));
+                    if (kFast) {
+                        isn[q] = h2u(__hmin2(m, u2h(p.HI2)));
+                        // Eq. 6c: sigma = +1 iff Is >= 0 iff bit 7 of the byte (bits 7 / 23)
+                        const uint32_t tsh = (j <= 8) ? (isn[q] << (8 - j)) : (isn[q] >> (j - 8));
+                        newW[lw] |= ~tsh & (kSignPair >> j);
                     } else {
-                        const uint32_t ge = __hge2_mask(v, u2h(p.I02));
-                        isn = (ge & p.I0MA2) | (~ge & h2u(m));
+                        const uint32_t ge = __hge2_mask(v, u2h(p.TOP2));
+                        isn[q] = (ge & p.HI2) | (~ge & h2u(m));
+                        IsR[g][q] = isn[q];
+                        // Eq. 6c: sigma = +1 iff Is >= 0 (sign bit clear; Is is never -0)
+                        newW[lw] |= (isn[q] & kSignPair) >> j;
                     }
-                    Is2[g][q] = isn;
-                    // Eq. 6c: sigma = +1 iff Is >= 0 (sign bit clear; Is is never -0)
-                    sgn[q] = isn & kSignPair;
-                    newW[lw] |= sgn[q] >> j;
                 }
-                uint4 b = fp8_bytes(sgn);
+                uint4 b;
+                if (kFast) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        pk[m] = __byte_perm(isn[2 * m], isn[2 * m + 1], 0x6420);
+                        IsR[g][m] = pk[m];
+                    }
+                    b.x = (~pk[0] & 0x80808080u) | 0x38383838u;
+                    b.y = (~pk[1] & 0x80808080u) | 0x38383838u;
+                    b.z = (~pk[2] & 0x80808080u) | 0x38383838u;
+                    b.w = (~pk[3] & 0x80808080u) | 0x38383838u;
+                } else {
+                    uint32_t sgn[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) sgn[q] = isn[q] & kSignPair;
+                    b = fp8_bytes(sgn);
+                }
                 if (i0 + 16 > a.N) b = mask_tail(b, i0, a.N);
                 *reinterpret_cast<uint4 *>(sA + cm_off(c, i0, Kp)) = b;
             }
-            if (energy && valid && ng > 0) atomicAdd(&eacc[c], static_cast<unsigned long long>(
+            if (energy && valid) atomicAdd(&eacc[c], static_cast<unsigned long long>(
                                                                       static_cast<long long>(esum)));
             tc_fence_before();
-            bar_sync(2, kThreads);
-            // all reads of the slot and all energy partials are done
+            // the slot path must finish every read of sigma(t - d) before any
+            // owner overwrites it; energy partials must all be in eacc
+            if (!kShfl || energy) bar_sync(2, kThreads);
             if (valid) {
                 if (update) {
 #pragma unroll
@@ -476,9 +541,10 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                         for (int q = 0; q < kMaxW; ++q) H[l][q] = H[l - 1][q];
 #pragma unroll
                     for (int q = 0; q < kMaxW; ++q) H[0][q] = newW[q];
+                    if (!kShfl)
 #pragma unroll
-                    for (int q = 0; q < kMaxW; ++q)
-                        if (2 * q < ng) slot[c * p.WP + w0 + q] = H[D][q];
+                        for (int q = 0; q < kMaxW; ++q)
+                            if (gran_of(2 * q) < p.G) slot[c * p.WP + part + 4 * q] = H[D][q];
                 }
                 if (energy && part == 0) {
                     const long long s = static_cast<long long>(eacc[c]);
@@ -493,6 +559,10 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
             }
             fence_proxy_async();
         }
+        if (++sub == a.tau) {
+            sub = 0;
+            if (++lvl > a.beta) lvl = 0;
+        }
         bar_sync(1, kThreads);
     }
 
@@ -502,15 +572,26 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         const int64_t ht = trial0 + lt;
 #pragma unroll
         for (int g = 0; g < kMaxG; ++g) {
-            if (g >= ng) continue;
-            const int i0 = (g0 + g) * 16;
+            const int gg = gran_of(g);
+            if (gg >= p.G) continue;
+            const int i0 = gg * 16;
             const int lw = g >> 1;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const float2 v = __half22float2(u2h(Is2[g][q]));
+                int32_t v0, v1;
+                if (kFast) {
+                    const uint32_t w = IsR[g][q >> 1];
+                    const int sh8 = (q & 1) * 16;
+                    v0 = int32_t((w >> sh8) & 0xFFu) - 128;
+                    v1 = int32_t((w >> (sh8 + 8)) & 0xFFu) - 128;
+                } else {
+                    const float2 v = __half22float2(u2h(IsR[g][q]));
+                    v0 = int32_t(v.x);
+                    v1 = int32_t(v.y);
+                }
                 const int i = i0 + 2 * q;
-                if (i < a.N) a.Is[gcol * a.N + i] = int32_t(v.x);
-                if (i + 1 < a.N) a.Is[gcol * a.N + i + 1] = int32_t(v.y);
+                if (i < a.N) a.Is[gcol * a.N + i] = v0;
+                if (i + 1 < a.N) a.Is[gcol * a.N + i + 1] = v1;
             }
             for (int e = 0; e < 16; ++e) {
                 const int i = i0 + e;
@@ -543,16 +624,19 @@ using KernelFn = void (*)(TcParams);
 
 // Kernel variants are split over several translation units (one per delay d)
 // so that they compile in parallel.
-KernelFn pick_d0(bool both, bool track, bool alpha1);
-KernelFn pick_d1(bool both, bool track, bool alpha1);
-KernelFn pick_d2(bool both, bool track, bool alpha1);
-KernelFn pick_d3(bool both, bool track, bool alpha1);
+KernelFn pick_d0(bool both, bool track, bool fast);
+KernelFn pick_d1(bool both, bool track, bool fast);
+KernelFn pick_d2(bool both, bool track, bool fast);
+KernelFn pick_d3(bool both, bool track, bool fast);
 
-#define SSQA_TC_DEFINE_PICK(DD)                                                                        \
-    KernelFn pick_d##DD(bool both, bool track, bool alpha1) {                                           \
-        if (DD == 1 && !both && !track && alpha1) return ssqa_tc_kernel<DD, false, false, (DD == 1)>;  \
+#define SSQA_TC_DEFINE_PICK(DD)                                                                          \
+    KernelFn pick_d##DD(bool both, bool track, bool fast) {                                               \
+        if (fast) {                                                                                       \
+            if (both) return track ? ssqa_tc_kernel<DD, true, true, true> : ssqa_tc_kernel<DD, true, false, true>; \
+            return track ? ssqa_tc_kernel<DD, false, true, true> : ssqa_tc_kernel<DD, false, false, true>;   \
+        }                                                                                                 \
         if (both) return track ? ssqa_tc_kernel<DD, true, true, false> : ssqa_tc_kernel<DD, true, false, false>; \
-        return track ? ssqa_tc_kernel<DD, false, true, false> : ssqa_tc_kernel<DD, false, false, false>;  \
+        return track ? ssqa_tc_kernel<DD, false, true, false> : ssqa_tc_kernel<DD, false, false, false>;     \
     }
 
 }  // namespace tc

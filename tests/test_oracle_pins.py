@@ -117,6 +117,15 @@ def test_philox_matches_independent_library():
         assert [int(x) for x in got] == want, c
 
 
+def test_noise_words_are_distinct_philox_outputs():
+    # every 32-spin word of a (replica, trial, cycle) reads a different
+    # (counter, output word) pair: no two words share random bits
+    seen = set()
+    for wd in range(64):
+        seen.add((4 * (wd // 16) + wd % 4, (wd // 4) % 4))
+    assert len(seen) == 64
+
+
 def test_noise_bits_balanced_and_distinct():
     # the per-spin bits are fair and differ across replica, trial and cycle
     bits = np.array([[O.noise_bit(5, i, k, 3, 17) for i in range(256)] for k in range(8)])
@@ -128,11 +137,12 @@ def test_noise_bits_balanced_and_distinct():
 
 
 def test_noise_bit_layout_definition():
-    # spin i: Philox(ctr=(i/128, k, trial, t)), word (i%128)/32, bit 15-e/2 (even e)
-    # or 31-(e-1)/2 (odd e), e = i % 32
+    # spin i, word w = i/32: Philox(ctr=(4(w/16) + w%4, k, trial, t)), output
+    # word (w/4)%4, bit 15-e/2 (even e) or 31-(e-1)/2 (odd e), e = i % 32
     seed, k, trial, t = 0x1234_5678_9ABC_DEF1, 2, 9, 44
-    for i in (0, 1, 2, 31, 32, 77, 127, 128, 300):
-        w = O.philox4x32_10([i // 128, k, trial, t], [seed & 0xFFFFFFFF, seed >> 32])[(i % 128) // 32]
+    for i in (0, 1, 2, 31, 32, 77, 127, 128, 300, 511, 512, 2049, 8191):
+        wd = i // 32
+        w = O.philox4x32_10([4 * (wd // 16) + wd % 4, k, trial, t], [seed & 0xFFFFFFFF, seed >> 32])[(wd // 4) % 4]
         e = i % 32
         b = 31 - (e >> 1) if e & 1 else 15 - (e >> 1)
         assert O.noise_bit(seed, i, k, trial, t) == (int(w) >> b) & 1

@@ -1,0 +1,71 @@
+"""Serving: requests of different sizes admitted by HBM budget and run
+concurrently give, each, exactly the result of the same anneal run alone."""
+import time
+
+import numpy as np
+import pytest
+
+import paper_2302_12454_gb300 as S
+from paper_2302_12454_gb300 import build as B
+from paper_2302_12454_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+
+
+def _gi(n, seed):
+    a = S.gen_er_graph(n, W.p_q32(0.3 + 0.4 * ((seed * 7) % 10) / 10), seed)
+    b, _ = S.permute_graph(a, seed + 1)
+    return S.Ising.gi(a, b)
+
+
+def test_mixed_requests_equal_alone():
+    rng = np.random.default_rng(41)
+    reqs = []
+    for j in range(14):
+        n = int(rng.integers(4, 21))
+        kw = dict(R=int(rng.choice([4, 8, 16])), cycles=int(rng.choice([100, 200, 300])),
+                  trials=int(rng.integers(1, 33)), seed=41 + j, tau=int(rng.choice([10, 25])))
+        if j % 5 == 3:
+            kw.update(delay=2, coupling=S.COUPLING_BOTH)
+        reqs.append((_gi(n, 100 + j), kw))
+    srv = S.Server(hbm_budget=1 << 30, max_slots=4)
+    tickets = [srv.submit(I, track_best=(j % 2 == 0), **kw) for j, (I, kw) in enumerate(reqs)]
+    results = {}
+    deadline = time.time() + 300
+    while len(results) < len(tickets) and time.time() < deadline:
+        for j, t in enumerate(tickets):
+            if j in results:
+                continue
+            r = srv.poll(t, timeout_ms=10)
+            if r is not None:
+                results[j] = r
+    assert len(results) == len(tickets)
+    for j, (I, kw) in enumerate(reqs):
+        alone = S.anneal(I, track_best=(j % 2 == 0), want_hist=True, **kw)
+        got, lat = results[j]
+        assert lat > 0
+        for k in alone:
+            np.testing.assert_array_equal(got[k], alone[k], err_msg=f"request {j} field {k}")
+    srv.close()
+
+
+def test_budget_and_ticket_errors():
+    srv = S.Server(hbm_budget=1 << 20, max_slots=2)
+    I = _gi(20, 3)
+    with pytest.raises(S.SSQAError) as e:
+        srv.submit(I, R=16, cycles=10, trials=512, seed=1)
+    assert e.value.code == S.ERR_BUDGET
+    import ctypes
+    assert S.lib().ssqa_poll(srv._s, 12345, None, 0, None) == S.ERR_NOT_FOUND
+    t = srv.submit(_gi(4, 1), R=2, cycles=5, trials=1, seed=1)
+    r = srv.poll(t, timeout_ms=-1)
+    assert r is not None
+    srv.close()
