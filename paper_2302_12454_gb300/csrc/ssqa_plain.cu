@@ -18,9 +18,10 @@
 namespace ssqa {
 namespace {
 
-constexpr int kSpins = 32;   // spins per block (one per lane)
-constexpr int kCols = 8;     // spin columns per block (one per warp)
-constexpr int kKT = 128;     // bytes of K staged per step
+constexpr int kSpins = 32;          // spins per block (one per lane)
+constexpr int kCols = 8;            // warps per block
+constexpr int kColsPerBlock = 32;   // spin columns per block (four per warp)
+constexpr int kKT = 128;            // bytes of K staged per step
 
 struct PlainState {
     int8_t *ring;     // [L][cols][Np] spin history, slot(t) = t mod L
@@ -76,70 +77,90 @@ __global__ void plain_init_kernel(AnnealArgs a, PlainState s) {
         }
 }
 
-// One synchronous update t -> t+1 of all (column c, spin i).
+// One synchronous update t -> t+1 of all (column c, spin i).  A block owns
+// 32 spins (one per lane) and 32 columns (four per warp): each J word staged
+// in shared memory feeds four dot products.  The host passes the cycle's
+// J_perp value and the history slots, so the kernel does no index division.
 template <bool kTrack>
-__global__ void __launch_bounds__(kSpins * kCols) plain_cycle_kernel(AnnealArgs a, PlainState s, int64_t t) {
+__global__ void __launch_bounds__(kSpins * kCols) plain_cycle_kernel(AnnealArgs a, int64_t cols, int64_t *e2acc,
+                                                                     uint32_t t, int32_t jp, const int8_t *cur,
+                                                                     const int8_t *old, int8_t *nxt) {
+    constexpr int kCPW = kColsPerBlock / kCols;  // columns per warp (thread)
     __shared__ uint32_t sJ[kSpins][kKT / 4 + 1];
-    __shared__ uint32_t sS[kCols][kKT / 4];
+    __shared__ __align__(16) uint32_t sS[kColsPerBlock][kKT / 4];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int32_t i = blockIdx.y * kSpins + lane;
-    const int64_t c = int64_t(blockIdx.x) * kCols + w;
-    const int64_t cols = s.cols;
-    const int8_t *cur = s.ring + slot_of(t, s.L) * cols * a.Np;
-    const int8_t *old = s.ring + slot_of(t - a.delay, s.L) * cols * a.Np;
-    int8_t *nxt = s.ring + slot_of(t + 1, s.L) * cols * a.Np;
+    const int32_t i = int32_t(blockIdx.y) * kSpins + lane;
+    const int64_t cb = int64_t(blockIdx.x) * kColsPerBlock;
+    const int Np = a.Np;
 
-    int32_t F = 0;
-    for (int32_t k0 = 0; k0 < a.Np; k0 += kKT) {
+    int32_t F[kCPW];
+#pragma unroll
+    for (int cc = 0; cc < kCPW; ++cc) F[cc] = 0;
+    for (int32_t k0 = 0; k0 < Np; k0 += kKT) {
         {
-            const int32_t row = blockIdx.y * kSpins + tid / 8;
+            const int32_t row = int32_t(blockIdx.y) * kSpins + tid / 8;
             const int32_t kk = k0 + (tid % 8) * 16;
             uint4 v = make_uint4(0, 0, 0, 0);
-            if (row < a.N && kk < a.Np) v = *reinterpret_cast<const uint4 *>(a.J_pad + int64_t(row) * a.Np + kk);
+            if (row < a.N && kk < Np) v = *reinterpret_cast<const uint4 *>(a.J_pad + int64_t(row) * Np + kk);
             uint32_t *d = &sJ[tid / 8][(tid % 8) * 4];
             d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
         }
-        if (tid < kCols * 8) {
-            const int64_t col = int64_t(blockIdx.x) * kCols + tid / 8;
+        {
+            const int64_t col = cb + tid / 8;
             const int32_t kk = k0 + (tid % 8) * 16;
             uint4 v = make_uint4(0, 0, 0, 0);
-            if (col < cols && kk < a.Np) v = *reinterpret_cast<const uint4 *>(cur + col * a.Np + kk);
+            if (col < cols && kk < Np) v = *reinterpret_cast<const uint4 *>(cur + col * Np + kk);
             *reinterpret_cast<uint4 *>(&sS[tid / 8][(tid % 8) * 4]) = v;
         }
         __syncthreads();
+#pragma unroll 8
+        for (int q = 0; q < kKT / 4; ++q) {
+            const int jw = int(sJ[lane][q]);
 #pragma unroll
-        for (int q = 0; q < kKT / 4; ++q) F = __dp4a(int(sJ[lane][q]), int(sS[w][q]), F);
+            for (int cc = 0; cc < kCPW; ++cc) F[cc] = __dp4a(jw, int(sS[w * kCPW + cc][q]), F[cc]);
+        }
         __syncthreads();
     }
 
-    const bool valid = i < a.N && c < cols;
-    int64_t e2 = 0;
-    if (valid) {
-        const int32_t k = int32_t(c % a.R);
-        const int64_t trial = c / a.R;
-        const int64_t base = c - k;  // column of replica 0 of this trial
-        const uint32_t nw = noise_word(a.seed, uint32_t(i), uint32_t(k), a.trial_offset + uint32_t(trial), uint32_t(t));
-        const int64_t r = ((nw >> spin_bit_pos(uint32_t(i))) & 1u) ? -1 : 1;
-        const int64_t period = int64_t(a.tau) * (a.beta + 1);
-        const int64_t jp = a.jperp_min + ((t % period) / a.tau) * int64_t(a.jperp_step);
-        // Eq. 6a: h + J sigma(t) + n_rnd r + J_perp(t) sigma_{k+1}(t - d)
-        int64_t cpl = old[(base + (k + 1) % a.R) * a.Np + i];
-        if (a.both) cpl += old[(base + (k + a.R - 1) % a.R) * a.Np + i];
-        const int64_t hi = a.h[i];
-        const int64_t I = hi + F + int64_t(a.n_rnd) * r + jp * cpl;
-        // Eq. 6b: saturating integral counter
-        const int64_t v = int64_t(a.Is[c * a.N + i]) + I;
-        const int32_t is_new = v >= a.I0 ? a.I0 - a.alpha : (v < -a.I0 ? -a.I0 : int32_t(v));
-        a.Is[c * a.N + i] = is_new;
-        // Eq. 6c
-        nxt[c * a.Np + i] = is_new >= 0 ? 1 : -1;
-        if (kTrack) e2 = -int64_t(cur[c * a.Np + i]) * (2 * hi + F);  // 2 E of sigma(t), Eq. 5
+    // noise words: lane cc computes the Philox call of column cc of this warp
+    uint32_t myw = 0;
+    {
+        const int64_t c = cb + w * kCPW + lane;
+        if (lane < kCPW && c < cols) {
+            const int32_t k = int32_t(c % a.R);
+            const uint32_t trial = a.trial_offset + uint32_t(c / a.R);
+            myw = noise_word(a.seed, uint32_t(blockIdx.y) * kSpins, uint32_t(k), trial, t);
+        }
     }
-    if (kTrack) {
 #pragma unroll
-        for (int o = 16; o; o >>= 1) e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
-        if (lane == 0 && c < cols) atomicAdd(reinterpret_cast<unsigned long long *>(&s.e2acc[c]),
-                                             static_cast<unsigned long long>(e2));
+    for (int cc = 0; cc < kCPW; ++cc) {
+        const int64_t c = cb + w * kCPW + cc;
+        const uint32_t nw = __shfl_sync(0xFFFFFFFFu, myw, cc);
+        const bool valid = i < a.N && c < cols;
+        int64_t e2 = 0;
+        if (valid) {
+            const int32_t k = int32_t(c % a.R);
+            const int64_t base = c - k;  // column of replica 0 of this trial
+            const int64_t r = ((nw >> spin_bit_pos(uint32_t(i))) & 1u) ? -1 : 1;
+            // Eq. 6a: h + J sigma(t) + n_rnd r + J_perp(t) sigma_{k+1}(t - d)
+            int64_t cpl = old[(base + (k + 1 == a.R ? 0 : k + 1)) * Np + i];
+            if (a.both) cpl += old[(base + (k == 0 ? a.R - 1 : k - 1)) * Np + i];
+            const int64_t hi = a.h[i];
+            const int64_t I = hi + F[cc] + int64_t(a.n_rnd) * r + int64_t(jp) * cpl;
+            // Eq. 6b: saturating integral counter
+            const int64_t v = int64_t(a.Is[c * a.N + i]) + I;
+            const int32_t is_new = v >= a.I0 ? a.I0 - a.alpha : (v < -a.I0 ? -a.I0 : int32_t(v));
+            a.Is[c * a.N + i] = is_new;
+            // Eq. 6c
+            nxt[c * Np + i] = is_new >= 0 ? 1 : -1;
+            if (kTrack) e2 = -int64_t(cur[c * Np + i]) * (2 * hi + F[cc]);  // 2 E of sigma(t), Eq. 5
+        }
+        if (kTrack) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
+            if (lane == 0 && c < cols)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&e2acc[c]), static_cast<unsigned long long>(e2));
+        }
     }
 }
 
@@ -265,17 +286,24 @@ int plain_anneal(const AnnealArgs &a, void *scratch, void *stream) {
     const int64_t t0 = a.start_cycle;
     plain_init_kernel<<<1024, 256, 0, st>>>(a, s);
     if (int rc = launch_check("plain init")) return rc;
-    const int64_t gx = (s.cols + kCols - 1) / kCols;
+    const int64_t gx = (s.cols + kColsPerBlock - 1) / kColsPerBlock;
     const int64_t gy = (a.N + kSpins - 1) / kSpins;
     if (gx > INT32_MAX || gy > 65535) return fail(SSQA_ERR_UNSUPPORTED, "plain path: problem exceeds the grid");
     const dim3 grid{unsigned(gx), unsigned(gy), 1u};
+    const int64_t period = int64_t(a.tau) * (a.beta + 1);
     for (int64_t c = 0; c < a.cycles; ++c) {
         const int64_t t = t0 + c;
+        const int32_t jp = a.jperp_min + int32_t((t % period) / a.tau) * a.jperp_step;  // Table 2 schedule
+        const int8_t *cur = s.ring + slot_of(t, s.L) * s.cols * a.Np;
+        const int8_t *old = s.ring + slot_of(t - a.delay, s.L) * s.cols * a.Np;
+        int8_t *nxt = s.ring + slot_of(t + 1, s.L) * s.cols * a.Np;
         if (a.track_best && c > 0) {
-            plain_cycle_kernel<true><<<grid, kSpins * kCols, 0, st>>>(a, s, t);
+            plain_cycle_kernel<true><<<grid, kSpins * kCols, 0, st>>>(a, s.cols, s.e2acc, uint32_t(t), jp, cur, old,
+                                                                       nxt);
             plain_best_kernel<<<256, 256, 0, st>>>(s.e2acc, 1, a.e_best, a.best_cycle, s.cols, int32_t(t));
         } else {
-            plain_cycle_kernel<false><<<grid, kSpins * kCols, 0, st>>>(a, s, t);
+            plain_cycle_kernel<false><<<grid, kSpins * kCols, 0, st>>>(a, s.cols, s.e2acc, uint32_t(t), jp, cur, old,
+                                                                        nxt);
         }
         if (int rc = launch_check("plain cycle")) return rc;
     }

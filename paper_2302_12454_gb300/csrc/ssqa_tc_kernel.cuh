@@ -207,9 +207,6 @@ __device__ __forceinline__ uint32_t word_bit(uint32_t w, uint32_t i) { return (w
 template <int D, bool kBoth, bool kTrack, bool kFast>
 __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_constant__ TcParams p) {
     constexpr bool kShfl = kFast;
-    // Loading the next granule's accumulators while computing the current one
-    // measured slower (it waits for the second MMA chunk earlier), so off.
-    constexpr bool kPrefetch = false;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = sm + p.smem_A;
@@ -424,27 +421,27 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
             for (int q = 0; q < kMaxW; ++q) newW[q] = 0u;
             float esum = 0.f;
             uint32_t up_w = 0, dn_w = 0;
-            uint32_t fb[kPrefetch ? 2 : 1][16];
-            if (kPrefetch && gran_of(0) < p.G) {
-                wait_chunk(gran_of(0) * 16);
-                tmem_ld16_issue(taddr_lane + uint32_t(gran_of(0) * 16), fb[0]);
-            }
+            // The second chunk's MMAs read every spin of A, so sigma(t+1) bytes of
+            // granules finished before they complete wait here (only the first
+            // four granule slots can lie in the first chunk, which is < 256 spins).
+            uint4 pend[4];
+            uint32_t pmask = 0;
+            auto flush_pending = [&]() {
+#pragma unroll
+                for (int g2 = 0; g2 < 4; ++g2)
+                    if (pmask & (1u << g2))
+                        *reinterpret_cast<uint4 *>(sA + cm_off(c, gran_of(g2) * 16, Kp)) = pend[g2];
+                pmask = 0;
+            };
 #pragma unroll
             for (int g = 0; g < kMaxG; ++g) {
                 const int gg = gran_of(g);
                 if (gg >= p.G) break;
-                uint32_t(&f)[16] = fb[kPrefetch ? (g & 1) : 0];
-                if (kPrefetch) {
-                    tmem_ld_wait(f);
-                    if (g + 1 < kMaxG && gran_of(g + 1) < p.G) {  // next granule loads while this one computes
-                        wait_chunk(gran_of(g + 1) * 16);
-                        tmem_ld16_issue(taddr_lane + uint32_t(gran_of(g + 1) * 16), fb[(g + 1) & 1]);
-                    }
-                } else {
-                    wait_chunk(gg * 16);
-                    tmem_ld16_issue(taddr_lane + uint32_t(gg * 16), f);
-                    tmem_ld_wait(f);
-                }
+                uint32_t f[16];
+                wait_chunk(gg * 16);
+                if (pmask && waited1) flush_pending();
+                tmem_ld16_issue(taddr_lane + uint32_t(gg * 16), f);
+                tmem_ld_wait(f);
                 const int i0 = gg * 16;
                 const int half = g & 1;
                 const int lw = g >> 1;
@@ -525,7 +522,16 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     b = fp8_bytes(sgn);
                 }
                 if (i0 + 16 > a.N) b = mask_tail(b, i0, a.N);
-                *reinterpret_cast<uint4 *>(sA + cm_off(c, i0, Kp)) = b;
+                if (g < 4 && p.nchunk > 1 && !waited1) {
+                    pend[g < 4 ? g : 0] = b;
+                    pmask |= 1u << g;
+                } else {
+                    *reinterpret_cast<uint4 *>(sA + cm_off(c, i0, Kp)) = b;
+                }
+            }
+            if (pmask) {
+                wait_chunk(p.crow[0]);
+                flush_pending();
             }
             if (energy && valid) atomicAdd(&eacc[c], static_cast<unsigned long long>(
                                                                       static_cast<long long>(esum)));

@@ -182,7 +182,11 @@ def test_batched_gi_n20_full_size_sampled_trials():
         np.testing.assert_array_equal(g["sigma"][tr], o["sigma"][0])
         np.testing.assert_array_equal(g["Is"][tr], o["Is"][0])
         np.testing.assert_array_equal(g["E_final"][tr], o["E_final"][0])
-    # every trial: energies consistent with the returned spins (any size)
+    # every trial: the plain CUDA path (per-cycle launches, int8 dot products)
+    # gives the same states, and energies match the returned spins
+    pl = S.anneal(I, algo=S.ALGO_PLAIN, **kw)
+    for k in ("sigma", "Is", "E_final"):
+        np.testing.assert_array_equal(g[k], pl[k])
     np.testing.assert_array_equal(S.energy(I, g["sigma"]), g["E_final"])
     assert (g["E_final"] >= -off).all()
     assert (g["Is"] >= -24).all() and (g["Is"] <= 23).all()
