@@ -57,10 +57,14 @@ extern "C" {
 #define SSQA_INIT_ALL_MINUS 1  /* sigma(0) = -1, Is = 0                              */
 #define SSQA_INIT_FROM_STATE 2 /* resume: sigma, sigma_hist and is_state are inputs */
 
-#define SSQA_ALGO_AUTO 0   /* tensor-core path when the instance allows it, else plain */
+#define SSQA_ALGO_AUTO 0   /* tensor-core path when the instance allows it, else delta */
 #define SSQA_ALGO_PLAIN 1  /* CUDA-core path, one kernel launch per cycle          */
 #define SSQA_ALGO_TENSOR 2 /* tcgen05 path, one persistent launch for all cycles;
                               SSQA_ERR_UNSUPPORTED if the instance does not fit     */
+#define SSQA_ALGO_DELTA 3  /* CUDA-core path keeping F = J sigma per column and, each
+                              cycle, adding only the flipped spins' columns of J (a
+                              dense recompute when many flip); AUTO picks it when the
+                              tensor path cannot take the instance                  */
 
 #define SSQA_FLAG_TRACK_BEST 1u  /* fill e_best / best_cycle                      */
 #define SSQA_FLAG_DEVICE_PTRS 2u /* state / result pointers are device pointers  */

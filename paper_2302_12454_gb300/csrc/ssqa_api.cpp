@@ -432,7 +432,7 @@ int validate(const ssqa_ising *I, const ssqa_params *p, const ssqa_result *r) {
     if (p->coupling != SSQA_COUPLING_UPPER && p->coupling != SSQA_COUPLING_BOTH)
         return fail(SSQA_ERR_INVALID_ARG, "unknown coupling mode");
     if (p->init_mode < 0 || p->init_mode > 2) return fail(SSQA_ERR_INVALID_ARG, "unknown init mode");
-    if (p->algo < 0 || p->algo > 2) return fail(SSQA_ERR_INVALID_ARG, "unknown algo");
+    if (p->algo < 0 || p->algo > 3) return fail(SSQA_ERR_INVALID_ARG, "unknown algo");
     if (p->start_cycle < 0 || int64_t(p->start_cycle) + p->cycles > 0xFFFFFFFEll)
         return fail(SSQA_ERR_INVALID_ARG, "cycle range must stay below 2^32 - 1");
     if (int64_t(p->trial_offset) + p->trials > 0xFFFFFFFFll)
@@ -550,10 +550,14 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     }
     if (use_tc) {
         rc = tc_anneal(I->tc, *dc, a, st);
-    } else {
+    } else if (p->algo == SSQA_ALGO_PLAIN) {
         DevBuf scratch;
         if ((e = alloc(scratch, plain_scratch_bytes(a)))) return cuda_fail(e, "ssqa_anneal: scratch allocation");
         rc = plain_anneal(a, scratch.p, st);
+    } else {
+        DevBuf scratch;
+        if ((e = alloc(scratch, delta_scratch_bytes(a)))) return cuda_fail(e, "ssqa_anneal: scratch allocation");
+        rc = delta_anneal(a, scratch.p, st);
     }
     if (rc) return rc;
     if (!devptr) {

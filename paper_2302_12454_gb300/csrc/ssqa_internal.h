@@ -99,6 +99,11 @@ size_t plain_scratch_bytes(const AnnealArgs &a);
 // plain_scratch_bytes(a) bytes of device memory (256-byte aligned).
 int plain_anneal(const AnnealArgs &a, void *scratch, void *stream);
 
+// Delta-field path: F = J sigma kept per column, sparse flip updates or a
+// dense recompute per cycle.  `scratch` holds delta_scratch_bytes(a) bytes.
+size_t delta_scratch_bytes(const AnnealArgs &a);
+int delta_anneal(const AnnealArgs &a, void *scratch, void *stream);
+
 // Energy E' of `count` spin rows of `pitch` bytes (device pointers), using
 // the zero-padded J rows (pitch Np).  No scratch.
 int energy_launch(const int8_t *J_pad, int32_t Np, const int32_t *h, int32_t N, const int8_t *sigma,

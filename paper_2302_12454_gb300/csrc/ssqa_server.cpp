@@ -47,7 +47,7 @@ struct Request {
 size_t footprint(const ssqa_ising *I, const ssqa_params &p) {
     const size_t N = size_t(I->N), cols = size_t(p.trials) * p.R;
     const size_t state = cols * N * (1 + 4 + size_t(p.delay)) + cols * 24;
-    const size_t scratch = size_t(p.delay + 2) * cols * ((N + 15) / 16 * 16) + cols * 16;
+    const size_t scratch = size_t(p.delay + 2) * cols * ((N + 15) / 16 * 16) + cols * N * 8 + cols * 32;
     const size_t instance = N * N * 2 + N * 8 + I->tc.b.size();
     return state + scratch + instance;
 }

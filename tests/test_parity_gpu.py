@@ -56,7 +56,7 @@ def assert_same(g, o, track=False):
 
 
 # ------------------------------------------------------------ full config 1
-@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN])
+@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN, S.ALGO_DELTA])
 def test_plain_gi_n6_full_bit_exact(algo):
     c = W.CONFIGS["plain_gi_n6"]
     I = gi(c["n"], c["p"], c["graph_seed"], c["perm_seed"])
@@ -84,7 +84,7 @@ VARIANTS = [
 ]
 
 
-@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN])
+@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN, S.ALGO_DELTA])
 @pytest.mark.parametrize("n,R,trials,cycles,extra", VARIANTS)
 def test_variants_bit_exact(algo, n, R, trials, cycles, extra):
     I = gi(n, 0.5, n, n + 1, toggle=(n % 2 == 1))
@@ -92,7 +92,7 @@ def test_variants_bit_exact(algo, n, R, trials, cycles, extra):
     assert_same(g, o, track=True)
 
 
-@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN])
+@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN, S.ALGO_DELTA])
 def test_zero_cycles_and_no_noise(algo):
     I = gi(6)
     g, o = both_runs(I, algo, R=4, cycles=0, trials=3, seed=5)
@@ -101,7 +101,7 @@ def test_zero_cycles_and_no_noise(algo):
     assert_same(g, o)
 
 
-@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN])
+@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN, S.ALGO_DELTA])
 @pytest.mark.parametrize("d", [0, 1, 2])
 def test_resume_equals_straight_run(algo, d):
     I = gi(8, 0.5, 4, 5)
@@ -185,8 +185,10 @@ def test_batched_gi_n20_full_size_sampled_trials():
     # every trial: the plain CUDA path (per-cycle launches, int8 dot products)
     # gives the same states, and energies match the returned spins
     pl = S.anneal(I, algo=S.ALGO_PLAIN, **kw)
+    de = S.anneal(I, algo=S.ALGO_DELTA, **kw)
     for k in ("sigma", "Is", "E_final"):
         np.testing.assert_array_equal(g[k], pl[k])
+        np.testing.assert_array_equal(g[k], de[k])
     np.testing.assert_array_equal(S.energy(I, g["sigma"]), g["E_final"])
     assert (g["E_final"] >= -off).all()
     assert (g["Is"] >= -24).all() and (g["Is"] <= 23).all()
