@@ -263,6 +263,12 @@ def run_ours(args, rank, world):
     }
     if rank == 0:
         out["clocks"] = clk.summary(int(os.environ.get("LOCAL_RANK", 0)))
+        # served latency: a seeded Poisson stream of GI requests (a bounded
+        # sample of the serving workload: n in [8, 20], R = 16, 32 trials)
+        from paper_2302_12454_gb300 import serving_bench as SB
+
+        out["served"] = SB.run(S, W, count=64, n_min=8, n_max=20, cycles_set=(500, 1000, 2000), slots=32,
+                               plain_sample=8)
         if not args.no_cpu_baseline:
             cores = min(16, os.cpu_count() or 1)
             rate, cwall = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, cycles, 2 * cores, cores)

@@ -153,11 +153,19 @@ typedef struct ssqa_params {
                              in its noise counters, so a run split over several
                              calls or devices equals one run                    */
     uint64_t seed;        /* Philox4x32-10 key (low word, high word)            */
+    int32_t i0_max;       /* I0 schedule of SSA (Sec. 4.4): 0 or I0 keeps I0 fixed
+                             (SSQA, Table 2); otherwise I0(t) = I0 * i0_mult^l,
+                             l = floor((t mod i0_tau L) / i0_tau), L levels up to
+                             i0_max = I0 * i0_mult^(L-1)                         */
+    int32_t i0_mult;      /*   1/beta of Sec. 4.4 (2 for beta = 0.5), >= 2     */
+    int32_t i0_tau;       /*   cycles per I0 level (tau = 10 in Sec. 4.4), >= 1 */
 } ssqa_params;
 
 /* Fill `p` with Table 2's constants at S = 12: I0 24, alpha 1, n_rnd 12,
  * J_perp 0 .. 6 in beta = 3 steps, tau = 100, d = 1, upper coupling, random
- * init, AUTO algorithm, no flags, R = 25 (Sec. 4.3), 1 trial, 0 cycles. */
+ * init, AUTO algorithm, no flags, R = 25 (Sec. 4.3), 1 trial, 0 cycles,
+ * fixed I0 (i0_max 0, i0_mult 2, i0_tau 10).  SSA (Eq. 2, Sec. 4.4) is the
+ * special case R = 1, J_perp = 0 with an I0 schedule. */
 void ssqa_params_default(ssqa_params *p);
 
 /* Outputs (and, with SSQA_INIT_FROM_STATE, inputs) of ssqa_anneal.  Layouts

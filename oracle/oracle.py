@@ -42,6 +42,7 @@ class Params(ctypes.Structure):
         ("beta", ctypes.c_int32), ("tau", ctypes.c_int32), ("delay", ctypes.c_int32),
         ("coupling_both", ctypes.c_int32), ("init_mode", ctypes.c_int32),
         ("start_cycle", ctypes.c_int32), ("seed", ctypes.c_uint64),
+        ("i0_max", ctypes.c_int32), ("i0_mult", ctypes.c_int32), ("i0_tau", ctypes.c_int32),
     ]
 
 
@@ -205,7 +206,7 @@ def ssa_i0(t, i0_min, i0_max, i0_mult, tau) -> int:
 # SSQA / SSA anneals (Eq. 6, Eq. 2)
 # --------------------------------------------------------------------------
 PAPER_DEFAULTS = dict(I0=24, alpha=1, n_rnd=12, jperp_min=0, jperp_max=6, beta=3, tau=100,
-                      delay=1, coupling_both=0, init_mode=0, start_cycle=0)
+                      delay=1, coupling_both=0, init_mode=0, start_cycle=0, i0_max=0, i0_mult=2, i0_tau=10)
 """Table 2 (J_perp 0..0.5, beta 3, d 1, I0 2, n_rnd 1) scaled by S = 12."""
 
 

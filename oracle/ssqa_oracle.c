@@ -356,6 +356,8 @@ double or_tts(double t, double p_s, double p_target)
 /* ------------------------------------------------------------------------- */
 /* SSQA, Eq. 6a-6c, all N*R spins of one trial updated synchronously.         */
 /* ------------------------------------------------------------------------- */
+int32_t or_ssa_i0(int64_t t, int32_t i0_min, int32_t i0_max, int32_t i0_mult, int32_t tau);
+
 typedef struct {
     int32_t N, R, cycles;
     int32_t I0, alpha, n_rnd;           /* scaled integers */
@@ -365,6 +367,7 @@ typedef struct {
     int32_t init_mode;                  /* 0 Philox, 1 all -1, 2 from state */
     int32_t start_cycle;                /* t of the first update */
     uint64_t seed;
+    int32_t i0_max, i0_mult, i0_tau;    /* I0 schedule of Sec. 4.4; i0_max 0 = fixed I0 */
 } or_params;
 
 /* One trial.  J, h: scaled integers (J zero diagonal, symmetric).
@@ -416,6 +419,9 @@ int or_anneal_trial(const or_params *p, const int64_t *h, const int64_t *J,
     for (c = 0; c < p->cycles; ++c) {
         int64_t t = (int64_t)p->start_cycle + c;
         int32_t jp = or_jperp(t, p->jperp_min, p->jperp_max, p->beta, p->tau);
+        /* Eq. 6b uses a fixed I0 (Table 2); with an I0 schedule (SSA, Sec. 4.4)
+         * the bound of cycle t is I0(t) */
+        int32_t I0 = p->i0_max > p->I0 ? or_ssa_i0(t, p->I0, p->i0_max, p->i0_mult, p->i0_tau) : p->I0;
         const int8_t *cur = ring;                         /* sigma(t)     */
         const int8_t *old = ring + (size_t)d * R * N;     /* sigma(t - d) */
         for (k = 0; k < R; ++k) {
@@ -434,10 +440,10 @@ int or_anneal_trial(const or_params *p, const int64_t *h, const int64_t *J,
                 /* Eq. 6b */
                 s_old = Is[(size_t)k * N + i];
                 v = s_old + I;
-                if (v >= p->I0)
-                    is_new = p->I0 - p->alpha;
-                else if (v < -p->I0)
-                    is_new = -p->I0;
+                if (v >= I0)
+                    is_new = I0 - p->alpha;
+                else if (v < -I0)
+                    is_new = -I0;
                 else
                     is_new = (int32_t)v;
                 Is_next[(size_t)k * N + i] = is_new;

@@ -37,6 +37,7 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_int32), ("delay", ctypes.c_int32), ("coupling", ctypes.c_int32),
         ("init_mode", ctypes.c_int32), ("algo", ctypes.c_int32), ("flags", ctypes.c_uint32),
         ("start_cycle", ctypes.c_int32), ("trial_offset", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+        ("i0_max", ctypes.c_int32), ("i0_mult", ctypes.c_int32), ("i0_tau", ctypes.c_int32),
     ]
 
 

@@ -1,7 +1,10 @@
-"""Command line: run SSQA anneals on a named synthetic workload.
+"""Command line: run SSQA anneals on a named synthetic workload, or measure
+served latency.
 
   python -m paper_2302_12454_gb300 anneal --workload batched_gi_n20 \\
-      [--cycles C] [--trials T] [--algo tensor|plain|auto] [--repeat K]
+      [--cycles C] [--trials T] [--algo tensor|plain|delta|auto] [--repeat K]
+  python -m paper_2302_12454_gb300 serve-bench [--requests 200] [--n-min 8]
+      [--n-max 20] [--cycles 1000,2000,5000] [--slots 32] [--load 0.8]
 
 Prints one line per run: device time of the anneal (CUDA events on the
 launching stream), spin-updates/s, success probability P_s (any replica at
@@ -64,6 +67,20 @@ def cmd_anneal(args):
         print(json.dumps(rec), flush=True)
 
 
+def cmd_serve(args):
+    import json as _json
+
+    import paper_2302_12454_gb300 as S
+    from paper_2302_12454_gb300 import build as B
+    from paper_2302_12454_gb300 import serving_bench as SB
+    from paper_2302_12454_gb300 import workloads as W
+
+    B.build()
+    out = SB.run(S, W, count=args.requests, n_min=args.n_min, n_max=args.n_max,
+                 cycles_set=tuple(int(c) for c in args.cycles.split(",")), slots=args.slots, load=args.load)
+    print(_json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2302_12454_gb300")
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -75,9 +92,18 @@ def main(argv=None):
     a.add_argument("--trials", type=int)
     a.add_argument("--algo", default="auto", choices=["auto", "tensor", "plain", "delta"])
     a.add_argument("--repeat", type=int, default=1)
+    sv = sub.add_parser("serve-bench", help="served p50/p99 latency under Poisson arrivals on cuda:0")
+    sv.add_argument("--requests", type=int, default=200)
+    sv.add_argument("--n-min", type=int, default=8)
+    sv.add_argument("--n-max", type=int, default=20)
+    sv.add_argument("--cycles", default="1000,2000,5000")
+    sv.add_argument("--slots", type=int, default=32)
+    sv.add_argument("--load", type=float, default=0.8)
     args = ap.parse_args(argv)
     if args.cmd == "anneal":
         cmd_anneal(args)
+    elif args.cmd == "serve-bench":
+        cmd_serve(args)
 
 
 if __name__ == "__main__":

@@ -24,6 +24,35 @@ int fail(int code, const std::string &msg) {
     return code;
 }
 
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = pools.find(dev);
+        if (it == pools.end()) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if ((e = cudaMemPoolCreate(&pool, &props))) return e;
+            int no = 0;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools.emplace(dev, pool);
+        } else {
+            pool = it->second;
+        }
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
 int check_device(int *device) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -397,6 +426,9 @@ void ssqa_params_default(ssqa_params *p) {
     p->coupling = SSQA_COUPLING_UPPER;
     p->init_mode = SSQA_INIT_RANDOM;
     p->algo = SSQA_ALGO_AUTO;
+    p->i0_max = 0;
+    p->i0_mult = 2;
+    p->i0_tau = 10;
 }
 
 double ssqa_tts(double t, double p_s, double p_target) {
@@ -444,6 +476,14 @@ int validate(const ssqa_ising *I, const ssqa_params *p, const ssqa_result *r) {
         return fail(SSQA_ERR_INVALID_ARG, "TRACK_BEST needs e_best and best_cycle");
     if (p->flags & ~(SSQA_FLAG_TRACK_BEST | SSQA_FLAG_DEVICE_PTRS))
         return fail(SSQA_ERR_INVALID_ARG, "unknown flag bits");
+    if (p->i0_max > p->I0) {
+        if (p->i0_mult < 2 || p->i0_tau < 1 || p->i0_max > 16383)
+            return fail(SSQA_ERR_INVALID_ARG, "I0 schedule: i0_mult >= 2, i0_tau >= 1, i0_max <= 16383");
+        int64_t v = p->I0;
+        while (v < p->i0_max) v *= p->i0_mult;
+        if (v != p->i0_max) return fail(SSQA_ERR_INVALID_ARG, "I0 schedule: i0_max must be I0 * i0_mult^m");
+        if (p->alpha > 2 * p->I0) return fail(SSQA_ERR_INVALID_ARG, "alpha must be in 1..2*I0");
+    }
     return SSQA_OK;
 }
 
@@ -492,6 +532,9 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     a.start_cycle = p->start_cycle;
     a.trial_offset = p->trial_offset;
     a.seed = p->seed;
+    a.i0_max = p->i0_max;
+    a.i0_mult = p->i0_mult;
+    a.i0_tau = p->i0_tau;
     a.track_best = p->flags & SSQA_FLAG_TRACK_BEST;
     a.J = dc->J;
     a.J_pad = dc->J_pad;
@@ -502,7 +545,7 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     DevBuf b_sig, b_hist, b_is, b_ef, b_eb, b_bc;
     auto alloc = [&](DevBuf &b, size_t bytes) -> cudaError_t {
         b.s = st;
-        return cudaMallocAsync(&b.p, bytes ? bytes : 1, st);
+        return dev_alloc(&b.p, bytes ? bytes : 1, st);
     };
     cudaError_t e;
     if (devptr) {
@@ -594,7 +637,7 @@ extern "C" int ssqa_energy(const ssqa_ising *I, const int8_t *sigma, int64_t cou
     DevBuf bs, be;
     bs.s = be.s = st;
     const size_t nb = size_t(count) * I->N;
-    if ((e = cudaMallocAsync(&bs.p, nb, st)) || (e = cudaMallocAsync(&be.p, size_t(count) * 8, st)))
+    if ((e = dev_alloc(&bs.p, nb, st)) || (e = dev_alloc(&be.p, size_t(count) * 8, st)))
         return cuda_fail(e, "ssqa_energy: allocation");
     if ((e = cudaMemcpyAsync(bs.p, sigma, nb, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "ssqa_energy: upload");
     rc = energy_launch(dc->J_pad, dc->Np, dc->h, I->N, static_cast<int8_t *>(bs.p), I->N, count,

@@ -44,7 +44,8 @@ __host__ __device__ inline int64_t slot_of(int64_t t, int32_t L) { return ((t % 
 // Eq. 6a-6c for all (column, spin) from the stored field; records flips.
 template <bool kTrack>
 __global__ void __launch_bounds__(kSp * kWarps) delta_update_kernel(AnnealArgs a, DeltaState s, uint32_t t, int32_t jp,
-                                                                    const int8_t *cur, const int8_t *old, int8_t *nxt,
+                                                                    int32_t I0, const int8_t *cur, const int8_t *old,
+                                                                    int8_t *nxt,
                                                                     int32_t *cnt_w, unsigned long long *total_w) {
     constexpr int kCPW = kCPB / kWarps;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kSp * kWarps) delta_update_kernel(AnnealArgs a
             // Eq. 6a-6c
             const int64_t I = hi + Fi + int64_t(a.n_rnd) * r + int64_t(jp) * cpl;
             const int64_t v = int64_t(a.Is[c * a.N + i]) + I;
-            const int32_t is_new = v >= a.I0 ? a.I0 - a.alpha : (v < -a.I0 ? -a.I0 : int32_t(v));
+            const int32_t is_new = v >= I0 ? I0 - a.alpha : (v < -I0 ? -I0 : int32_t(v));
             a.Is[c * a.N + i] = is_new;
             const int8_t s_old = cur[c * Np + i];
             const int8_t s_new = is_new >= 0 ? 1 : -1;
@@ -309,6 +310,7 @@ int delta_anneal(const AnnealArgs &a, void *scratch, void *stream) {
         const int64_t t = t0 + c;
         const int par = int(c & 1);  // update writes cnt/total[1 - par]... see below
         const int32_t jp = a.jperp_min + int32_t((t % period) / a.tau) * a.jperp_step;
+        const int32_t I0 = i0_at(a, t);
         const int8_t *cur = s.ring + slot_of(t, s.L) * s.cols * a.Np;
         const int8_t *old = s.ring + slot_of(t - a.delay, s.L) * s.cols * a.Np;
         int8_t *nxt = s.ring + slot_of(t + 1, s.L) * s.cols * a.Np;
@@ -318,11 +320,11 @@ int delta_anneal(const AnnealArgs &a, void *scratch, void *stream) {
         int32_t *cnt_w = s.cnt + wp * s.cols;
         int32_t *cnt_o = s.cnt + (1 - wp) * s.cols;
         if (a.track_best && c > 0) {
-            delta_update_kernel<true><<<grid, kSp * kWarps, 0, st>>>(a, s, uint32_t(t), jp, cur, old, nxt, cnt_w,
+            delta_update_kernel<true><<<grid, kSp * kWarps, 0, st>>>(a, s, uint32_t(t), jp, I0, cur, old, nxt, cnt_w,
                                                                      s.total + wp);
             delta_best_kernel<<<256, 256, 0, st>>>(s.e2acc, 1, a.e_best, a.best_cycle, s.cols, int32_t(t));
         } else {
-            delta_update_kernel<false><<<grid, kSp * kWarps, 0, st>>>(a, s, uint32_t(t), jp, cur, old, nxt, cnt_w,
+            delta_update_kernel<false><<<grid, kSp * kWarps, 0, st>>>(a, s, uint32_t(t), jp, I0, cur, old, nxt, cnt_w,
                                                                       s.total + wp);
         }
         if (int rc = launch_check("delta update")) return rc;

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "ssqa.h"
 
 namespace ssqa {
@@ -78,6 +80,7 @@ struct AnnealArgs {
     int32_t delay, both, init_mode, start_cycle;
     uint32_t trial_offset;
     uint64_t seed;
+    int32_t i0_max, i0_mult, i0_tau;  // I0 schedule (i0_max <= I0: fixed)
     bool track_best;
     // instance
     const int8_t *J;
@@ -112,6 +115,23 @@ int energy_launch(const int8_t *J_pad, int32_t Np, const int32_t *h, int32_t N, 
 // Tensor-core path: whether the resident kernel can run this problem.
 bool tc_supported(const TcImage &img, const AnnealArgs &a, std::string *why);
 int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream);
+
+// I0 of cycle t: fixed, or the SSA schedule of Sec. 4.4.
+inline int32_t i0_at(const AnnealArgs &a, int64_t t) {
+    if (a.i0_max <= a.I0) return a.I0;
+    int32_t levels = 1;
+    for (int64_t v = a.I0; v < a.i0_max; v *= a.i0_mult) ++levels;
+    const int64_t l = (t % (int64_t(a.i0_tau) * levels)) / a.i0_tau;
+    int64_t v = a.I0;
+    for (int64_t q = 0; q < l; ++q) v *= a.i0_mult;
+    return int32_t(v);
+}
+
+// Stream-ordered allocation from the library's own pool on the current device.
+// The pool never inserts waits between streams to reuse memory (only memory
+// whose free has already completed is reused), so concurrent anneals on
+// different streams stay independent.
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
 
 // Current device has compute capability 10.x (sm_100 family).
 int check_device(int *device);

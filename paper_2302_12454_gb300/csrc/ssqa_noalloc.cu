@@ -64,6 +64,12 @@ int check_params(int32_t N, const ssqa_params *p, const ssqa_result *r) {
         return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: R in 1..128, trials >= 1, cycles >= 0");
     if (p->I0 < 1 || p->I0 > 16383 || p->alpha < 1 || p->alpha > 2 * p->I0 || p->n_rnd < 0 || p->n_rnd > (1 << 20))
         return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: I0, alpha or n_rnd out of range");
+    if (p->i0_max > p->I0) {
+        int64_t v = p->I0;
+        while (p->i0_mult >= 2 && v < p->i0_max) v *= p->i0_mult;
+        if (p->i0_mult < 2 || p->i0_tau < 1 || v != p->i0_max || p->i0_max > 16383)
+            return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: bad I0 schedule");
+    }
     if (p->beta < 1 || p->tau < 1 || (int64_t(p->jperp_max) - p->jperp_min) % p->beta ||
         p->jperp_min < -(1 << 20) || p->jperp_min > (1 << 20) || p->jperp_max < -(1 << 20) || p->jperp_max > (1 << 20))
         return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: bad J_perp schedule");
@@ -108,6 +114,9 @@ extern "C" int ssqa_anneal_noalloc(int32_t N, const int8_t *J_padded, const int3
     a.start_cycle = p.start_cycle;
     a.trial_offset = p.trial_offset;
     a.seed = p.seed;
+    a.i0_max = p.i0_max;
+    a.i0_mult = p.i0_mult;
+    a.i0_tau = p.i0_tau;
     a.track_best = (p.flags & SSQA_FLAG_TRACK_BEST) != 0;
     a.J = J_padded;
     a.J_pad = J_padded;

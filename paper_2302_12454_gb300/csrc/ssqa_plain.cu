@@ -83,8 +83,9 @@ __global__ void plain_init_kernel(AnnealArgs a, PlainState s) {
 // J_perp value and the history slots, so the kernel does no index division.
 template <bool kTrack>
 __global__ void __launch_bounds__(kSpins * kCols) plain_cycle_kernel(AnnealArgs a, int64_t cols, int64_t *e2acc,
-                                                                     uint32_t t, int32_t jp, const int8_t *cur,
-                                                                     const int8_t *old, int8_t *nxt) {
+                                                                     uint32_t t, int32_t jp, int32_t I0,
+                                                                     const int8_t *cur, const int8_t *old,
+                                                                     int8_t *nxt) {
     constexpr int kCPW = kColsPerBlock / kCols;  // columns per warp (thread)
     __shared__ uint32_t sJ[kSpins][kKT / 4 + 1];
     __shared__ __align__(16) uint32_t sS[kColsPerBlock][kKT / 4];
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(kSpins * kCols) plain_cycle_kernel(AnnealArgs 
             const int64_t I = hi + F[cc] + int64_t(a.n_rnd) * r + int64_t(jp) * cpl;
             // Eq. 6b: saturating integral counter
             const int64_t v = int64_t(a.Is[c * a.N + i]) + I;
-            const int32_t is_new = v >= a.I0 ? a.I0 - a.alpha : (v < -a.I0 ? -a.I0 : int32_t(v));
+            const int32_t is_new = v >= I0 ? I0 - a.alpha : (v < -I0 ? -I0 : int32_t(v));
             a.Is[c * a.N + i] = is_new;
             // Eq. 6c
             nxt[c * Np + i] = is_new >= 0 ? 1 : -1;
@@ -294,16 +295,17 @@ int plain_anneal(const AnnealArgs &a, void *scratch, void *stream) {
     for (int64_t c = 0; c < a.cycles; ++c) {
         const int64_t t = t0 + c;
         const int32_t jp = a.jperp_min + int32_t((t % period) / a.tau) * a.jperp_step;  // Table 2 schedule
+        const int32_t I0 = i0_at(a, t);
         const int8_t *cur = s.ring + slot_of(t, s.L) * s.cols * a.Np;
         const int8_t *old = s.ring + slot_of(t - a.delay, s.L) * s.cols * a.Np;
         int8_t *nxt = s.ring + slot_of(t + 1, s.L) * s.cols * a.Np;
         if (a.track_best && c > 0) {
-            plain_cycle_kernel<true><<<grid, kSpins * kCols, 0, st>>>(a, s.cols, s.e2acc, uint32_t(t), jp, cur, old,
-                                                                       nxt);
+            plain_cycle_kernel<true><<<grid, kSpins * kCols, 0, st>>>(a, s.cols, s.e2acc, uint32_t(t), jp, I0, cur,
+                                                                       old, nxt);
             plain_best_kernel<<<256, 256, 0, st>>>(s.e2acc, 1, a.e_best, a.best_cycle, s.cols, int32_t(t));
         } else {
-            plain_cycle_kernel<false><<<grid, kSpins * kCols, 0, st>>>(a, s.cols, s.e2acc, uint32_t(t), jp, cur, old,
-                                                                        nxt);
+            plain_cycle_kernel<false><<<grid, kSpins * kCols, 0, st>>>(a, s.cols, s.e2acc, uint32_t(t), jp, I0, cur,
+                                                                        old, nxt);
         }
         if (int rc = launch_check("plain cycle")) return rc;
     }

@@ -7,7 +7,10 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 
 #include "ssqa_tc_kernel.cuh"
 
@@ -29,6 +32,23 @@ uint32_t half2_bits(float v) {
     uint32_t u;
     std::memcpy(&u, &h, 4);
     return u;
+}
+
+// Every variant is configured once with the largest shared-memory carveout
+// and opt-in size, so that launches for instances of different sizes (for
+// example concurrent server requests) never need a different SM carveout.
+void configure_once(KernelFn fn) {
+    static std::mutex mu;
+    static std::set<std::pair<int, KernelFn>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, fn})) return;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared));
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    done.insert({dev, fn});
 }
 
 struct Layout {
@@ -55,7 +75,8 @@ bool plan(const TcImage &img, const AnnealArgs &a, Layout *L, std::string *why) 
     }
     const int64_t jpmax = std::max<int64_t>(std::llabs(int64_t(a.jperp_min)),
                                             std::llabs(int64_t(a.jperp_min) + int64_t(a.jperp_step) * a.beta));
-    if (int64_t(a.I0) + a.n_rnd + (a.both ? 2 : 1) * jpmax > 1024) {
+    const int64_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
+    if (i0_top + a.n_rnd + (a.both ? 2 : 1) * jpmax > 1024) {
         *why = "I0 + n_rnd + |J_perp| terms exceed the exact FP16 epilogue range (1024)";
         return false;
     }
@@ -133,11 +154,17 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.NR2 = half2_bits(float(a.n_rnd));
     // fast variant: R divides 32, counters fit a biased byte, alpha = 1, and
     // a fresh start (resumed counters may lie outside the byte range)
-    const bool fast = (32 % a.R == 0) && a.I0 <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
-    const float bias = fast ? 1152.f : 0.f;
-    p.LO2 = half2_bits(bias - float(a.I0));
-    p.HI2 = half2_bits(bias + float(a.I0 - a.alpha));
-    p.TOP2 = half2_bits(bias + float(a.I0));
+    const int32_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
+    const bool fast = (32 % a.R == 0) && i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
+    p.bias = fast ? 1152.f : 0.f;
+    p.i0_levels = 1;
+    p.i0_mult = 2;
+    p.i0_tau = 1 << 30;
+    if (a.i0_max > a.I0) {
+        for (int64_t v = a.I0; v < a.i0_max; v *= a.i0_mult) ++p.i0_levels;
+        p.i0_mult = a.i0_mult;
+        p.i0_tau = a.i0_tau;
+    }
     p.smem_A = L.smem_A;
     p.smem_B = L.smem_B;
     p.smem_slot = L.smem_slot;
@@ -147,12 +174,12 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int *err = nullptr;
-    cudaError_t e = cudaMallocAsync(&err, sizeof(int), st);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&err), sizeof(int), st);
     if (e) return fail(SSQA_ERR_OOM, std::string("tensor path: ") + cudaGetErrorString(e));
     cudaMemsetAsync(err, 0, sizeof(int), st);
     p.err = err;
     KernelFn fn = pick(a.delay, a.both != 0, a.track_best, fast);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    configure_once(fn);
     const int64_t grid = (int64_t(a.trials) + L.Tb - 1) / L.Tb;
     fn<<<unsigned(grid), kThreads, L.total, st>>>(p);
     e = cudaGetLastError();

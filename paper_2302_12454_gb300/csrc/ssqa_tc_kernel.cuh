@@ -57,7 +57,8 @@ struct TcParams {
     uint32_t tmem_cols;
     uint8_t a_w[kMaxNh];
     uint32_t JM2, NR2;
-    uint32_t LO2, HI2, TOP2;  // bias - I0, bias + I0 - alpha, bias + I0 (half2)
+    float bias;                // counter offset of the FP16 epilogue
+    int32_t i0_levels, i0_mult, i0_tau;  // I0 schedule (1 level: fixed I0)
     int32_t smem_A, smem_B, smem_slot, smem_h, smem_e, smem_bar;
     int *err;
 };
@@ -373,6 +374,13 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     const int64_t period = int64_t(a.tau) * (a.beta + 1);
     int sub = int((int64_t(a.start_cycle) % period) % a.tau);
     int lvl = int((int64_t(a.start_cycle) % period) / a.tau);
+    // I0 of Eq. 6b: fixed (Table 2) or the SSA schedule of Sec. 4.4, tracked
+    // the same way
+    const int64_t iperiod = int64_t(p.i0_tau) * p.i0_levels;
+    int isub = int((int64_t(a.start_cycle) % iperiod) % p.i0_tau);
+    int ilvl = int((int64_t(a.start_cycle) % iperiod) / p.i0_tau);
+    int i0cur = a.I0;
+    for (int q = 0; q < ilvl; ++q) i0cur *= p.i0_mult;
     for (int it = 0; it < iters; ++it) {
         const int64_t t = int64_t(a.start_cycle) + it;
         const bool update = it < a.cycles;
@@ -398,6 +406,10 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         {
             const float jpf = float(a.jperp_min + lvl * a.jperp_step);
             const uint32_t JP2 = h2u(__floats2half2_rn(jpf, jpf));
+            const float i0f = float(i0cur);
+            const uint32_t LO2 = h2u(__floats2half2_rn(p.bias - i0f, p.bias - i0f));
+            const uint32_t HI2 = h2u(__floats2half2_rn(p.bias + i0f - float(a.alpha), p.bias + i0f - float(a.alpha)));
+            const uint32_t TOP2 = h2u(__floats2half2_rn(p.bias + i0f, p.bias + i0f));
             bool waited0 = false, waited1 = false;
             auto wait_chunk = [&](int i0) {
                 const int ch = (p.nchunk > 1 && i0 >= p.crow[0]) ? 1 : 0;
@@ -489,15 +501,15 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     const uint32_t ib = kFast ? __byte_perm(IsR[g][q >> 1], 0x64646464u, (q & 1) ? 0x4342 : 0x4140)
                                               : IsR[g][q];
                     const __half2 v = __hadd2(u2h(ib), y);
-                    const __half2 m = __hmax2(v, u2h(p.LO2));
+                    const __half2 m = __hmax2(v, u2h(LO2));
                     if (kFast) {
-                        isn[q] = h2u(__hmin2(m, u2h(p.HI2)));
+                        isn[q] = h2u(__hmin2(m, u2h(HI2)));
                         // Eq. 6c: sigma = +1 iff Is >= 0 iff bit 7 of the byte (bits 7 / 23)
                         const uint32_t tsh = (j <= 8) ? (isn[q] << (8 - j)) : (isn[q] >> (j - 8));
                         newW[lw] |= ~tsh & (kSignPair >> j);
                     } else {
-                        const uint32_t ge = __hge2_mask(v, u2h(p.TOP2));
-                        isn[q] = (ge & p.HI2) | (~ge & h2u(m));
+                        const uint32_t ge = __hge2_mask(v, u2h(TOP2));
+                        isn[q] = (ge & HI2) | (~ge & h2u(m));
                         IsR[g][q] = isn[q];
                         // Eq. 6c: sigma = +1 iff Is >= 0 (sign bit clear; Is is never -0)
                         newW[lw] |= (isn[q] & kSignPair) >> j;
@@ -568,6 +580,15 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         if (++sub == a.tau) {
             sub = 0;
             if (++lvl > a.beta) lvl = 0;
+        }
+        if (++isub == p.i0_tau) {
+            isub = 0;
+            if (++ilvl == p.i0_levels) {
+                ilvl = 0;
+                i0cur = a.I0;
+            } else {
+                i0cur *= p.i0_mult;
+            }
         }
         bar_sync(1, kThreads);
     }

@@ -407,3 +407,20 @@ def test_ssqa_finds_planted_ground_state_small():
     h, J, off = O.build_gi_ising(a, b)
     out = O.anneal(h, J, R=8, cycles=400, trials=8, seed=33)
     assert (out["E_final"].min(axis=1) == -off).mean() >= 0.5
+
+
+def test_ssa_schedule_is_ssqa_r1_with_i0_schedule():
+    # SSA of Sec. 4.4 (I0 from 1 to 16, x2 every 10 cycles, n_rnd = 1) at
+    # scale S = 4: I0' = 4 .. 64, n_rnd' = 4.  The Eq. 6 loop with R = 1,
+    # J_perp = 0 and the same I0 schedule reproduces the Eq. 2 implementation.
+    a = O.gen_er_graph(6, 1 << 31, 41)
+    b, _ = O.permute_graph(a, 42)
+    h, J, off = O.build_gi_ising(a, b, S=4)
+    q = O.anneal(h, J, R=1, cycles=230, trials=1, seed=43, trial_offset=2, jperp_max=0,
+                 I0=4, alpha=1, n_rnd=4, i0_max=64, i0_mult=2, i0_tau=10)
+    s, Is = O.ssa(h, J, cycles=230, seed=43, trial=2, i0_min=4, i0_max=64, i0_mult=2, tau=10, alpha=1, n_rnd=4)
+    assert np.array_equal(q["sigma"][0, 0], s)
+    assert np.array_equal(q["Is"][0, 0], Is)
+    # the schedule matters: a fixed I0 gives a different trajectory
+    f = O.anneal(h, J, R=1, cycles=230, trials=1, seed=43, trial_offset=2, jperp_max=0, I0=4, alpha=1, n_rnd=4)
+    assert not np.array_equal(f["Is"], q["Is"])

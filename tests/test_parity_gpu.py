@@ -217,3 +217,28 @@ def test_large_instances_transition_sampled(kind):
     np.testing.assert_array_equal(nxt["sigma"][tr], o["sigma"][0])
     np.testing.assert_array_equal(nxt["Is"][tr], o["Is"][0])
     np.testing.assert_array_equal(nxt["E_final"][tr], o["E_final"][0])
+
+
+# ------------------------------------------------- SSA mode (Eq. 2, Sec. 4.4)
+@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN, S.ALGO_DELTA])
+def test_ssa_mode_matches_eq2(algo):
+    # R = 1, J_perp = 0, I0 from 1 to 16 doubling every 10 cycles (scale 4)
+    a = S.gen_er_graph(8, W.p_q32(0.5), 51)
+    b, _ = S.permute_graph(a, 52)
+    I = S.Ising.gi(a, b, 1, 1, 4)
+    h, J, off = I.export()
+    g = S.anneal(I, R=1, cycles=300, trials=6, seed=53, algo=algo, jperp_max=0, I0=4, alpha=1, n_rnd=4,
+                 i0_max=64, i0_mult=2, i0_tau=10)
+    for tr in range(6):
+        s, Is = O.ssa(h, J, cycles=300, seed=53, trial=tr, i0_min=4, i0_max=64, i0_mult=2, tau=10, alpha=1,
+                      n_rnd=4)
+        np.testing.assert_array_equal(g["sigma"][tr, 0], s)
+        np.testing.assert_array_equal(g["Is"][tr, 0], Is)
+
+
+@pytest.mark.parametrize("algo", [S.ALGO_TENSOR, S.ALGO_PLAIN, S.ALGO_DELTA])
+def test_ssqa_with_i0_schedule_bit_exact(algo):
+    I = gi(9, 0.5, 61, 62)
+    g, o = both_runs(I, algo, R=8, cycles=120, trials=5, seed=63, tau=7, I0=12, i0_max=96, i0_mult=2, i0_tau=9,
+                     track=True)
+    assert_same(g, o, track=True)
