@@ -15,6 +15,9 @@
 
 #include <climits>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "philox.cuh"
 #include "ssqa_internal.h"
@@ -84,8 +87,9 @@ __global__ void __launch_bounds__(kSp * kWarps) delta_update_kernel(AnnealArgs a
             const int8_t s_new = is_new >= 0 ? 1 : -1;
             nxt[c * Np + i] = s_new;
             if (s_new != s_old) {
+                // entry: spin index, sign bit set when the spin became -1
                 const int32_t idx = atomicAdd(&cnt_w[c], 1);
-                s.list[c * a.N + idx] = i;
+                s.list[c * a.N + idx] = s_new > 0 ? i : int32_t(uint32_t(i) | 0x80000000u);
                 ++flips;
             }
             if (kTrack) e2 = -int64_t(s_old) * (2 * hi + Fi);
@@ -161,15 +165,25 @@ __global__ void __launch_bounds__(kSp * kWarps) delta_apply_kernel(AnnealArgs a,
         const int64_t c = cb + w * kCPW + cc;
         if (c >= s.cols || i >= a.N) continue;
         const int32_t n = cnt_r[c];
-        int32_t Fi = s.F[c * a.N + i];
+        if (n == 0) continue;
         const int32_t *lst = s.list + c * a.N;
-        for (int32_t q = 0; q < n; ++q) {
-            const int32_t j = lst[q];
-            // sigma_j went from -s to s: F += 2 s J_ij  (J_ij = J_ji, row j)
-            const int32_t sj = nxt[c * Np + j];
-            Fi += 2 * sj * int32_t(a.J_pad[int64_t(j) * Np + i]);
+        const int8_t *Jc = a.J_pad + i;
+        // sigma_j went from -s to s: F_i += 2 s J_ij  (J_ij = J_ji, row j)
+        int32_t d0 = 0, d1 = 0;
+        int32_t q = 0;
+        for (; q + 1 < n; q += 2) {
+            const uint32_t e0 = uint32_t(lst[q]), e1 = uint32_t(lst[q + 1]);
+            const int32_t v0 = Jc[int64_t(e0 & 0x7FFFFFFFu) * Np];
+            const int32_t v1 = Jc[int64_t(e1 & 0x7FFFFFFFu) * Np];
+            d0 += (e0 >> 31) ? -v0 : v0;
+            d1 += (e1 >> 31) ? -v1 : v1;
         }
-        s.F[c * a.N + i] = Fi;
+        if (q < n) {
+            const uint32_t e0 = uint32_t(lst[q]);
+            const int32_t v0 = Jc[int64_t(e0 & 0x7FFFFFFFu) * Np];
+            d0 += (e0 >> 31) ? -v0 : v0;
+        }
+        s.F[c * a.N + i] += 2 * (d0 + d1);
     }
 }
 
@@ -263,6 +277,67 @@ inline int launch_check(const char *what) {
 
 inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Probe flip lists: every column lists spins 0..m-1 as flipped.
+__global__ void delta_probe_kernel(DeltaState s, int32_t N, int32_t m, int32_t *cnt) {
+    for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < s.cols * int64_t(m);
+         x += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = x / m;
+        const int32_t q = int32_t(x % m);
+        s.list[c * N + q] = q;
+        if (q == 0) cnt[c] = m;
+    }
+}
+
+// Autotuned dense/sparse switch: on the first anneal of a shape (N, columns)
+// one dense pass and one sparse pass with N/16 flips per column are timed
+// with CUDA events on the launching stream; the cycle then goes dense once
+// its total flips cost more, by that measurement, than a dense pass.
+unsigned long long dense_threshold(const AnnealArgs &a, const DeltaState &s, dim3 grid, cudaStream_t st) {
+    static std::mutex mu;
+    static std::map<std::pair<int64_t, int64_t>, unsigned long long> cache;
+    const auto key = std::make_pair(int64_t(a.N), s.cols);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    unsigned long long thr = (unsigned long long)(s.cols) * (unsigned long long)(a.N) / 4ull + 1ull;
+    const int32_t m = a.N >= 16 ? a.N / 16 : 1;
+    cudaEvent_t e0, e1, e2, e3;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1) || cudaEventCreate(&e2) || cudaEventCreate(&e3)) {
+        cudaGetLastError();
+        return thr;
+    }
+    int8_t *spins = s.ring;  // any spin slot: the probes only read it
+    unsigned long long *tot = s.total;
+    const unsigned long long dense_now = 0ull, never = ~0ull;
+    cudaMemsetAsync(s.F, 0, size_t(s.cols) * size_t(a.N) * 4, st);
+    cudaMemsetAsync(spins, 0, size_t(s.cols) * size_t(a.Np), st);
+    cudaMemsetAsync(tot, 0, 16, st);
+    delta_probe_kernel<<<1024, 256, 0, st>>>(s, a.N, m, s.cnt);
+    cudaEventRecord(e0, st);
+    delta_apply_kernel<<<grid, kSp * kWarps, 0, st>>>(a, s, spins, s.cnt, s.cnt + s.cols, tot, tot + 1, dense_now);
+    cudaEventRecord(e1, st);
+    delta_probe_kernel<<<1024, 256, 0, st>>>(s, a.N, m, s.cnt);
+    cudaEventRecord(e2, st);
+    delta_apply_kernel<<<grid, kSp * kWarps, 0, st>>>(a, s, spins, s.cnt, s.cnt + s.cols, tot, tot + 1, never);
+    cudaEventRecord(e3, st);
+    float t_dense = 0.f, t_sparse = 0.f;
+    if (cudaEventSynchronize(e3) == cudaSuccess && cudaEventElapsedTime(&t_dense, e0, e1) == cudaSuccess &&
+        cudaEventElapsedTime(&t_sparse, e2, e3) == cudaSuccess && t_sparse > 0.f) {
+        const double per_flip = double(t_sparse) / (double(s.cols) * m);
+        thr = (unsigned long long)(double(t_dense) / per_flip) + 1ull;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    cudaEventDestroy(e3);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = thr;
+    return thr;
+}
+
 }  // namespace
 
 size_t delta_scratch_bytes(const AnnealArgs &a) {
@@ -294,11 +369,7 @@ int delta_anneal(const AnnealArgs &a, void *scratch, void *stream) {
     const int64_t gx = (s.cols + kCPB - 1) / kCPB, gy = (a.N + kSp - 1) / kSp;
     if (gx > INT32_MAX || gy > 65535) return fail(SSQA_ERR_UNSUPPORTED, "delta path: problem exceeds the grid");
     const dim3 grid{unsigned(gx), unsigned(gy), 1u};
-    // Dense recompute once the flips would cost more than one dense pass.
-    // Per flip and column the sparse update does about N adds with scattered
-    // byte loads; a dense pass is N^2 / 4 dp4a per column, so the crossover is
-    // near a quarter of the spins flipping.
-    const unsigned long long dense_at = (unsigned long long)(s.cols) * (unsigned long long)(a.N) / 4ull + 1ull;
+    const unsigned long long dense_at = dense_threshold(a, s, grid, st);
     delta_init_kernel<<<1024, 256, 0, st>>>(a, s);
     if (int rc = launch_check("delta init")) return rc;
     // F(t0) = J sigma(t0): dense (total[0] starts saturated)
