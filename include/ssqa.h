@@ -57,14 +57,19 @@ extern "C" {
 #define SSQA_INIT_ALL_MINUS 1  /* sigma(0) = -1, Is = 0                              */
 #define SSQA_INIT_FROM_STATE 2 /* resume: sigma, sigma_hist and is_state are inputs */
 
-#define SSQA_ALGO_AUTO 0   /* tensor-core path when the instance allows it, else delta */
+#define SSQA_ALGO_AUTO 0   /* resident tensor path (N <= 512), else the streamed
+                              tensor path (N > 256), else delta                     */
 #define SSQA_ALGO_PLAIN 1  /* CUDA-core path, one kernel launch per cycle          */
-#define SSQA_ALGO_TENSOR 2 /* tcgen05 path, one persistent launch for all cycles;
-                              SSQA_ERR_UNSUPPORTED if the instance does not fit     */
+#define SSQA_ALGO_TENSOR 2 /* tcgen05 paths, one persistent launch for all cycles:
+                              resident when the instance fits one SM, else
+                              streamed; SSQA_ERR_UNSUPPORTED if neither can take it */
 #define SSQA_ALGO_DELTA 3  /* CUDA-core path keeping F = J sigma per column and, each
                               cycle, adding only the flipped spins' columns of J (a
-                              dense recompute when many flip); AUTO picks it when the
-                              tensor path cannot take the instance                  */
+                              dense recompute when many flip); AUTO picks it when no
+                              tensor path can take the instance                     */
+#define SSQA_ALGO_STREAMED 4 /* the streamed tcgen05 path only (N > 256): J streamed
+                              from L2 in 256-spin chunks, clusters of up to 8 CTAs
+                              per 128 spin columns; SSQA_ERR_UNSUPPORTED otherwise   */
 
 #define SSQA_FLAG_TRACK_BEST 1u  /* fill e_best / best_cycle                      */
 #define SSQA_FLAG_DEVICE_PTRS 2u /* state / result pointers are device pointers  */
@@ -202,8 +207,9 @@ typedef struct ssqa_result {
  *   calls return after the results are in host memory; device-pointer calls
  *   (SSQA_FLAG_DEVICE_PTRS) only enqueue work on the stream.
  * Errors: SSQA_ERR_INVALID_ARG (parameter out of range, missing buffer),
- * SSQA_ERR_UNSUPPORTED (SSQA_ALGO_TENSOR forced on an instance whose
- * couplings or size the tensor path cannot take exactly), SSQA_ERR_OOM,
+ * SSQA_ERR_UNSUPPORTED (SSQA_ALGO_TENSOR or SSQA_ALGO_STREAMED forced on an
+ * instance whose couplings or size the tensor paths cannot take exactly, or
+ * SSQA_ALGO_STREAMED with resumed counters outside -128..127), SSQA_ERR_OOM,
  * SSQA_ERR_DEVICE (no usable GPU, launch or kernel failure). */
 int ssqa_anneal(const ssqa_ising *ising, const ssqa_params *params, ssqa_result *out,
                 void *cuda_stream);

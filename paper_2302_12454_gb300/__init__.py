@@ -19,7 +19,7 @@ OK, PENDING = 0, 1
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, ERR_DEVICE, ERR_NOT_FOUND = -1, -2, -3, -4, -5, -6, -7
 COUPLING_UPPER, COUPLING_BOTH = 0, 1
 INIT_RANDOM, INIT_ALL_MINUS, INIT_FROM_STATE = 0, 1, 2
-ALGO_AUTO, ALGO_PLAIN, ALGO_TENSOR, ALGO_DELTA = 0, 1, 2, 3
+ALGO_AUTO, ALGO_PLAIN, ALGO_TENSOR, ALGO_DELTA, ALGO_STREAMED = 0, 1, 2, 3, 4
 FLAG_TRACK_BEST, FLAG_DEVICE_PTRS = 1, 2
 
 

@@ -46,7 +46,8 @@ def cmd_anneal(args):
     I, has_ground = _instance(S, W, cfg)
     h, J, off = I.export()
     N, R, T = h.shape[0], cfg["R"], cfg["trials"]
-    algo = {"auto": S.ALGO_AUTO, "tensor": S.ALGO_TENSOR, "plain": S.ALGO_PLAIN, "delta": S.ALGO_DELTA}[args.algo]
+    algo = {"auto": S.ALGO_AUTO, "tensor": S.ALGO_TENSOR, "plain": S.ALGO_PLAIN, "delta": S.ALGO_DELTA,
+            "streamed": S.ALGO_STREAMED}[args.algo]
     p = S.make_params(R=R, cycles=cfg["cycles"], trials=T, seed=cfg["seed"], tau=cfg["tau"], algo=algo)
     sig = torch.empty((T, R, N), dtype=torch.int8, device="cuda")
     Is = torch.empty((T, R, N), dtype=torch.int32, device="cuda")
@@ -90,7 +91,7 @@ def main(argv=None):
     a.add_argument("--workload", default="batched_gi_n20", choices=sorted(W.CONFIGS))
     a.add_argument("--cycles", type=int)
     a.add_argument("--trials", type=int)
-    a.add_argument("--algo", default="auto", choices=["auto", "tensor", "plain", "delta"])
+    a.add_argument("--algo", default="auto", choices=["auto", "tensor", "plain", "delta", "streamed"])
     a.add_argument("--repeat", type=int, default=1)
     sv = sub.add_parser("serve-bench", help="served p50/p99 latency under Poisson arrivals on cuda:0")
     sv.add_argument("--requests", type=int, default=200)

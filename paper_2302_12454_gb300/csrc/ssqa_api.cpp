@@ -151,6 +151,51 @@ void prepare_tc(ssqa_ising *I) {
     t.nh = nh;
     t.N16 = (N + 15) / 16 * 16;
     t.Kp = (t.N16 + nh + 31) / 32 * 32;
+    // accumulator bound: every partial sum of D stays an exact small integer
+    for (int i = 0; i < N; ++i) {
+        int64_t s = std::llabs(t.h_unit[i]);
+        for (int j = 0; j < N; ++j) s += std::llabs(I->J[size_t(i) * N + j] / g);
+        if (s > 16384) {
+            t.why = "row sums of |J|/jm + |h|/jm exceed 2^14";
+            return;
+        }
+    }
+    for (size_t i = 0; i < size_t(N) * N; ++i)
+        if (I->J[i] && e4m3_of_int(I->J[i] / g) < 0) {
+            t.why = "a coupling J/jm has no exact FP8 E4M3 value";
+            return;
+        }
+    t.a_w.assign(nh, 0);
+    for (int m = 0; m < nh; ++m) t.a_w[m] = uint8_t(e4m3_of_int(m == 0 ? 1 : (m == 1 ? 16 : 256)));
+    auto hdigit = [&](int i, int m) -> uint8_t {
+        const int64_t hv = t.h_unit[i];
+        const int sgn = hv < 0 ? -1 : 1;
+        const int64_t a = std::llabs(hv);
+        int64_t d;
+        if (m == 0) d = a % 16;
+        else if (m == 1) d = (a / 16) % 16;
+        else d = std::max<int64_t>(0, std::min<int64_t>(15, a / 256 - int64_t(m - 2) * 15));
+        return uint8_t(e4m3_of_int(sgn * d));
+    };
+    if (N > 256 && nh <= 16) {
+        // streamed image: 256-spin chunks x 32-wide K-blocks
+        t.KB = t.Kp / 32;
+        t.NCH = (t.N16 + 255) / 256;
+        t.bs.assign(size_t(t.NCH) * t.KB * 8192, 0);
+        auto boff = [&](int i, int k) -> size_t {
+            const int ch = i / 256, r = i % 256, kb = k / 32, kk = k % 32;
+            return (size_t(ch) * t.KB + kb) * 8192 + size_t(r / 8) * 256 + size_t(kk / 16) * 128 + size_t(r % 8) * 16 +
+                   size_t(kk % 16);
+        };
+        for (int i = 0; i < N; ++i) {
+            for (int j = 0; j < N; ++j) {
+                const int8_t v = I->J[size_t(i) * N + j];
+                if (v) t.bs[boff(i, j)] = uint8_t(e4m3_of_int(v / g));
+            }
+            for (int m = 0; m < nh; ++m) t.bs[boff(i, t.N16 + m)] = hdigit(i, m);
+        }
+        t.s_ok = true;
+    }
     if (N <= 256) {
         t.nchunk = 1;
         t.chunk_rows[0] = t.N16;
@@ -164,15 +209,6 @@ void prepare_tc(ssqa_ising *I) {
         return;
     }
     t.Brows = t.chunk_rows[0] + t.chunk_rows[1];
-    // accumulator bound: every partial sum of D stays an exact small integer
-    for (int i = 0; i < N; ++i) {
-        int64_t s = std::llabs(t.h_unit[i]);
-        for (int j = 0; j < N; ++j) s += std::llabs(I->J[size_t(i) * N + j] / g);
-        if (s > 16384) {
-            t.why = "row sums of |J|/jm + |h|/jm exceed 2^14";
-            return;
-        }
-    }
     const int Kp = t.Kp;
     auto off = [Kp](int r, int k) -> size_t {
         return size_t(r / 8) * (size_t(Kp) * 8) + size_t(k / 16) * 128 + size_t(r % 8) * 16 + size_t(k % 16);
@@ -190,23 +226,8 @@ void prepare_tc(ssqa_ising *I) {
             }
             t.b[off(i, j)] = uint8_t(code);
         }
-    t.a_w.assign(nh, 0);
-    for (int m = 0; m < nh; ++m) t.a_w[m] = uint8_t(e4m3_of_int(m == 0 ? 1 : (m == 1 ? 16 : 256)));
-    for (int i = 0; i < N; ++i) {
-        int64_t hv = t.h_unit[i];
-        int sgn = hv < 0 ? -1 : 1;
-        int64_t a = std::llabs(hv);
-        for (int m = 0; m < nh; ++m) {
-            int64_t d;
-            if (m == 0) d = a % 16;
-            else if (m == 1) d = (a / 16) % 16;
-            else {
-                int64_t rest = a / 256 - int64_t(m - 2) * 15;
-                d = std::max<int64_t>(0, std::min<int64_t>(15, rest));
-            }
-            t.b[off(i, t.N16 + m)] = uint8_t(e4m3_of_int(sgn * d));
-        }
-    }
+    for (int i = 0; i < N; ++i)
+        for (int m = 0; m < nh; ++m) t.b[off(i, t.N16 + m)] = hdigit(i, m);
     t.ok = true;
 }
 
@@ -244,6 +265,8 @@ int device_copy(const ssqa_ising *cI, DeviceCopy **out) {
         cudaFree(dc.h);
         cudaFree(dc.tc_b);
         cudaFree(dc.tc_h_unit);
+        cudaFree(dc.tcs_b);
+        cudaFree(dc.tcs_hf);
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? SSQA_ERR_OOM : SSQA_ERR_DEVICE,
                     std::string("instance upload: ") + cudaGetErrorString(e));
@@ -257,6 +280,14 @@ int device_copy(const ssqa_ising *cI, DeviceCopy **out) {
     if ((e = cudaMemset(dc.J_pad, 0, N * dc.Np))) return bad(e);
     if ((e = cudaMemcpy2D(dc.J_pad, dc.Np, I->J.data(), N, N, N, cudaMemcpyHostToDevice))) return bad(e);
     if ((e = cudaMemcpy(dc.h, I->h.data(), N * 4, cudaMemcpyHostToDevice))) return bad(e);
+    if (I->tc.s_ok) {
+        if ((e = cudaMalloc(&dc.tcs_b, I->tc.bs.size()))) return bad(e);
+        if ((e = cudaMemcpy(dc.tcs_b, I->tc.bs.data(), I->tc.bs.size(), cudaMemcpyHostToDevice))) return bad(e);
+        std::vector<float> hf(N);
+        for (size_t i = 0; i < N; ++i) hf[i] = float(I->tc.h_unit[i]);
+        if ((e = cudaMalloc(&dc.tcs_hf, N * 4))) return bad(e);
+        if ((e = cudaMemcpy(dc.tcs_hf, hf.data(), N * 4, cudaMemcpyHostToDevice))) return bad(e);
+    }
     if (I->tc.ok) {
         if ((e = cudaMalloc(&dc.tc_b, I->tc.b.size()))) return bad(e);
         if ((e = cudaMemcpy(dc.tc_b, I->tc.b.data(), I->tc.b.size(), cudaMemcpyHostToDevice))) return bad(e);
@@ -394,6 +425,8 @@ void ssqa_ising_free(ssqa_ising *I) {
         cudaFree(kv.second.h);
         cudaFree(kv.second.tc_b);
         cudaFree(kv.second.tc_h_unit);
+        cudaFree(kv.second.tcs_b);
+        cudaFree(kv.second.tcs_hf);
     }
     cudaSetDevice(cur);
     cudaGetLastError();
@@ -464,7 +497,7 @@ int validate(const ssqa_ising *I, const ssqa_params *p, const ssqa_result *r) {
     if (p->coupling != SSQA_COUPLING_UPPER && p->coupling != SSQA_COUPLING_BOTH)
         return fail(SSQA_ERR_INVALID_ARG, "unknown coupling mode");
     if (p->init_mode < 0 || p->init_mode > 2) return fail(SSQA_ERR_INVALID_ARG, "unknown init mode");
-    if (p->algo < 0 || p->algo > 3) return fail(SSQA_ERR_INVALID_ARG, "unknown algo");
+    if (p->algo < 0 || p->algo > 4) return fail(SSQA_ERR_INVALID_ARG, "unknown algo");
     if (p->start_cycle < 0 || int64_t(p->start_cycle) + p->cycles > 0xFFFFFFFEll)
         return fail(SSQA_ERR_INVALID_ARG, "cycle range must stay below 2^32 - 1");
     if (int64_t(p->trial_offset) + p->trials > 0xFFFFFFFFll)
@@ -583,21 +616,33 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
         }
     }
 
-    std::string why;
-    bool use_tc = false;
-    if (p->algo == SSQA_ALGO_TENSOR) {
-        if (!tc_supported(I->tc, a, &why)) return fail(SSQA_ERR_UNSUPPORTED, "tensor path: " + why);
-        use_tc = true;
-    } else if (p->algo == SSQA_ALGO_AUTO) {
+    std::string why, why_s;
+    bool use_tc = false, use_tcs = false;
+    if (p->algo == SSQA_ALGO_STREAMED) {
+        use_tcs = tcs_supported(I->tc, a, &why_s);
+        if (!use_tcs) return fail(SSQA_ERR_UNSUPPORTED, "streamed tensor path: " + why_s);
+    } else if (p->algo == SSQA_ALGO_TENSOR || p->algo == SSQA_ALGO_AUTO) {
         use_tc = tc_supported(I->tc, a, &why);
+        if (!use_tc) use_tcs = tcs_supported(I->tc, a, &why_s);
+        if (p->algo == SSQA_ALGO_TENSOR && !use_tc && !use_tcs)
+            return fail(SSQA_ERR_UNSUPPORTED, "tensor path: " + why + "; streamed tensor path: " + why_s);
     }
+    bool done = false;
     if (use_tc) {
         rc = tc_anneal(I->tc, *dc, a, st);
-    } else if (p->algo == SSQA_ALGO_PLAIN) {
+        done = true;
+    } else if (use_tcs) {
+        DevBuf scratch;
+        if ((e = alloc(scratch, tcs_scratch_bytes(I->tc, a)))) return cuda_fail(e, "ssqa_anneal: scratch allocation");
+        rc = tcs_anneal(I->tc, *dc, a, scratch.p, st);
+        // a resumed state the byte counters cannot hold falls back to the CUDA-core paths
+        done = !(rc == SSQA_ERR_UNSUPPORTED && p->algo == SSQA_ALGO_AUTO);
+    }
+    if (!done && p->algo == SSQA_ALGO_PLAIN) {
         DevBuf scratch;
         if ((e = alloc(scratch, plain_scratch_bytes(a)))) return cuda_fail(e, "ssqa_anneal: scratch allocation");
         rc = plain_anneal(a, scratch.p, st);
-    } else {
+    } else if (!done) {
         DevBuf scratch;
         if ((e = alloc(scratch, delta_scratch_bytes(a)))) return cuda_fail(e, "ssqa_anneal: scratch allocation");
         rc = delta_anneal(a, scratch.p, st);

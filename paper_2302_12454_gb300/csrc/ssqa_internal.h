@@ -42,6 +42,12 @@ struct TcImage {
     std::vector<uint8_t> b;   // B image, Brows * Kp bytes
     std::vector<uint8_t> a_w; // e4m3 weights of the h columns (nh bytes)
     std::vector<int32_t> h_unit; // h_i / jm (N)
+    // Streamed image (instances too large for one SM): B in 256-spin chunks
+    // and 32-wide K-blocks, block (ch, kb) of 256 x 32 bytes at
+    // (ch * KB + kb) * 8192, element (r, k) at (r/8)*256 + (k/16)*128 + (r%8)*16 + k%16.
+    bool s_ok = false;
+    int32_t KB = 0, NCH = 0;
+    std::vector<uint8_t> bs;
 };
 
 struct DeviceCopy {
@@ -51,6 +57,8 @@ struct DeviceCopy {
     int32_t *h = nullptr;      // N int32
     uint8_t *tc_b = nullptr;   // B image
     int32_t *tc_h_unit = nullptr;
+    uint8_t *tcs_b = nullptr;  // streamed B image
+    float *tcs_hf = nullptr;   // h / jm as float
 };
 
 }  // namespace ssqa
@@ -132,6 +140,11 @@ inline int32_t i0_at(const AnnealArgs &a, int64_t t) {
 // whose free has already completed is reused), so concurrent anneals on
 // different streams stay independent.
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
+
+// Streamed tensor-core path (N too large for the resident kernel).
+bool tcs_supported(const TcImage &img, const AnnealArgs &a, std::string *why);
+size_t tcs_scratch_bytes(const TcImage &img, const AnnealArgs &a);
+int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *scratch, void *stream);
 
 // Current device has compute capability 10.x (sm_100 family).
 int check_device(int *device);

@@ -45,10 +45,14 @@ struct Request {
 };
 
 size_t footprint(const ssqa_ising *I, const ssqa_params &p) {
-    const size_t N = size_t(I->N), cols = size_t(p.trials) * p.R;
+    const size_t N = size_t(I->N), cols = size_t(p.trials) * p.R, Np = (N + 15) / 16 * 16;
     const size_t state = cols * N * (1 + 4 + size_t(p.delay)) + cols * 24;
-    const size_t scratch = size_t(p.delay + 2) * cols * ((N + 15) / 16 * 16) + cols * N * 8 + cols * 32;
-    const size_t instance = N * N * 2 + N * 8 + I->tc.b.size();
+    // the larger of the CUDA-core scratch and the streamed path's operand slots
+    const size_t scratch_cc = size_t(p.delay + 2) * cols * Np + cols * N * 8 + cols * 32;
+    const size_t groups = (size_t(p.trials) + 128 / p.R - 1) / (128 / p.R);
+    const size_t scratch_s = groups * size_t(p.delay + 2) * size_t(I->tc.KB) * 4096 + cols * Np + cols * 32 + 1024;
+    const size_t scratch = scratch_cc > scratch_s ? scratch_cc : scratch_s;
+    const size_t instance = N * N * 2 + N * 12 + I->tc.b.size() + I->tc.bs.size();
     return state + scratch + instance;
 }
 

@@ -1,0 +1,670 @@
+// Streamed tensor-core path of SSQA for sm_103a, for instances whose
+// operands do not fit in one SM (N > 400).
+//
+// A CTA owns 128 spin columns (whole trials, as in the resident kernel) and a
+// share of the spin chunks (256 spins each) of the field product
+//   D[c][i] = sum_j sigma_{j,c}(t) J_ij / jm + h_i / jm     (Eq. 6a, exact FP8)
+// A thread-block cluster of CS CTAs covers all chunks of one column group;
+// chunk ch belongs to cluster rank ch mod CS.  Per cycle:
+//   producer warp  streams, for each owned chunk, the K-blocks of A (sigma(t)
+//                  of the 128 columns, 4 KB) and B (J rows of the chunk, 8 KB)
+//                  from L2 into a 12-stage shared-memory ring (bulk async
+//                  copies completing on mbarriers);
+//   MMA warp       issues one tcgen05.mma kind::f8f6f4 (M 128, N <= 256, K 32)
+//                  per stage into one of two TMEM accumulators;
+//   8 epilogue warps turn a finished accumulator into sigma(t+1) of the chunk
+//                  (Eq. 6a-6c, the same packed-half2 arithmetic as the resident
+//                  kernel) while the next chunk's MMAs run;
+// and a cluster barrier closes the cycle.  sigma lives in L2 as FP8 operand
+// blocks, one slot per history level (the replica term reads the ring
+// neighbour's sigma(t - d) from its slot), and the counters as bytes Is + 128.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <utility>
+
+#include "ssqa_tc_kernel.cuh"
+
+namespace ssqa {
+namespace tcs {
+using namespace tc;
+
+constexpr int kStages = 12;
+constexpr int kABytes = 128 * 32;   // one K-block of A
+constexpr int kBBytes = 256 * 32;   // one K-block of a B chunk
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kEpi = 8;             // epilogue warps (2 per TMEM lane quadrant)
+constexpr int kThr = (2 + kEpi) * 32;
+
+struct SParams {
+    AnnealArgs a;
+    const uint8_t *B;       // [NCH][KB][256 x 32] blocks
+    uint8_t *A;             // [groups][L][KB][128 x 32] blocks
+    uint8_t *IsB;           // [cols][Np] counters + 128
+    const float *hf;        // h / jm as float (N)
+    unsigned long long *eacc;  // [2][cols]
+    int64_t *ebest, *efin;     // [cols]
+    int32_t *bcyc;             // [cols]
+    int *err;
+    int32_t N16, KB, NCH, L, CS, Tb, jm, last_rows;
+    uint32_t NR2, JM2;
+    float bias;
+    int32_t i0_levels, i0_mult, i0_tau;
+};
+
+// --------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Byte offset of (row r, k) inside one 32-byte-wide K-block (core matrices).
+__device__ __forceinline__ uint32_t blk_off(int r, int k) {
+    return uint32_t((r >> 3) * 256 + ((k >> 4) & 1) * 128 + (r & 7) * 16 + (k & 15));
+}
+__device__ __forceinline__ int64_t slot_of(int64_t t, int32_t L) { return ((t % L) + L) % L; }
+
+// ------------------------------------------------------------------- kernel
+template <bool kTrack>
+__global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant__ SParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *ring = sm;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kStages * kStageBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *tfull = empty + kStages;   // [2]
+    uint64_t *tempty = tfull + 2;        // [2]
+    uint64_t *drain = tempty + 2;        // [1]
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
+
+    const AnnealArgs &a = p.a;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rank = int(cluster_rank());
+    const int64_t grp = blockIdx.x / p.CS;
+    const int64_t trial0 = grp * p.Tb;
+    const int ntr = int(a.trials - trial0 < p.Tb ? a.trials - trial0 : p.Tb);
+    const int vcols = ntr * a.R;
+    const int64_t col0 = trial0 * a.R;
+    const bool need_final = a.e_final != nullptr || kTrack;
+    const int iters = a.cycles + (need_final ? 1 : 0);
+    const int nmine = (p.NCH - rank + p.CS - 1) / p.CS;  // chunks rank, rank + CS, ...
+    const int64_t cols = int64_t(a.trials) * a.R;
+    uint8_t *Ag = p.A + grp * int64_t(p.L) * p.KB * kABytes;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpi);
+        }
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_holder, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+    // A failed bounded wait (or the flag set by another CTA) stops all work;
+    // every thread still passes every cluster barrier, so the exit is uniform.
+    bool abort_run = false;
+    uint32_t nis = 0;  // producer: stage fills issued
+
+    // pipeline positions carried across cycles
+    int ps = 0, pph = 1;   // producer: stage, empty-barrier parity (first pass free)
+    int ms = 0, mph = 0;   // MMA: stage, full-barrier parity
+    uint32_t mt_ph = 3u;   // MMA: tmem-empty parity per buffer (bit b)
+    uint32_t et_ph = 0u;   // epilogue: tmem-full parity per buffer (bit b)
+
+    // epilogue identity: TMEM lane quadrant qd (column c), part 0 / 1 of the words
+    const int ew = warp - 2;
+    const int qd = warp & 3, part = ew >> 2;
+    const int c = qd * 32 + lane;
+    const bool valid = warp >= 2 && c < vcols;
+    const int lt = valid ? c / a.R : 0, k = valid ? c % a.R : 0;
+    const uint32_t trial_g = a.trial_offset + uint32_t(trial0 + lt);
+    const int nb_up = lt * a.R + (k + 1) % a.R;
+    const int nb_dn = lt * a.R + (k + a.R - 1) % a.R;
+    const int64_t gcol = col0 + c;
+    int64_t e_best = LLONG_MAX;
+    int32_t best_cycle = -1;
+
+    const int64_t period = int64_t(a.tau) * (a.beta + 1);
+    int sub = int((int64_t(a.start_cycle) % period) % a.tau);
+    int lvl = int((int64_t(a.start_cycle) % period) / a.tau);
+    const int64_t iperiod = int64_t(p.i0_tau) * p.i0_levels;
+    int isub = int((int64_t(a.start_cycle) % iperiod) % p.i0_tau);
+    int ilvl = int((int64_t(a.start_cycle) % iperiod) / p.i0_tau);
+    int i0cur = a.I0;
+    for (int q = 0; q < ilvl; ++q) i0cur *= p.i0_mult;
+
+    for (int it = 0; it < iters; ++it) {
+        const int64_t t = int64_t(a.start_cycle) + it;
+        const bool update = it < a.cycles;
+        const bool energy = (kTrack && it > 0) || !update;
+        const uint8_t *Acur = Ag + slot_of(t, p.L) * p.KB * kABytes;
+        if (*reinterpret_cast<volatile int *>(p.err)) abort_run = true;
+        if (warp == 0) {
+            // ---------------------------------------------------- producer
+            if (lane == 0 && !abort_run) {
+                fence_async_global();
+                for (int m = 0; m < nmine && !abort_run; ++m) {
+                    const int ch = rank + m * p.CS;
+                    const uint8_t *Bc = p.B + int64_t(ch) * p.KB * kBBytes;
+                    if (m > 0 && *reinterpret_cast<volatile int *>(p.err)) abort_run = true;
+                    for (int kb = 0; kb < p.KB && !abort_run; ++kb) {
+                        if (!mbar_wait(&empty[ps], uint32_t(pph))) {
+                            atomicExch(p.err, 1);
+                            abort_run = true;
+                            break;
+                        }
+                        uint8_t *st = ring + ps * kStageBytes;
+                        mbar_expect_tx(&full[ps], kStageBytes);
+                        bulk_g2s(st, Acur + int64_t(kb) * kABytes, kABytes, &full[ps]);
+                        bulk_g2s(st + kABytes, Bc + int64_t(kb) * kBBytes, kBBytes, &full[ps]);
+                        ++nis;
+                        if (++ps == kStages) {
+                            ps = 0;
+                            pph ^= 1;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        } else if (warp == 1) {
+            // ------------------------------------------------------- MMA
+            if (lane == 0 && !abort_run) {
+                for (int m = 0; m < nmine && !abort_run; ++m) {
+                    const int ch = rank + m * p.CS;
+                    const int b = m & 1;
+                    const int rows = ch == p.NCH - 1 ? p.last_rows : 256;
+                    const uint32_t idesc = (1u << 4) | (uint32_t(rows >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+                    if (m > 0 && *reinterpret_cast<volatile int *>(p.err)) abort_run = true;
+                    if (abort_run || !mbar_wait(&tempty[b], (mt_ph >> b) & 1u)) {
+                        if (!abort_run) atomicExch(p.err, 1);
+                        abort_run = true;
+                        break;
+                    }
+                    mt_ph ^= 1u << b;
+                    tc_fence_after();
+                    for (int kb = 0; kb < p.KB; ++kb) {
+                        if (!mbar_wait(&full[ms], uint32_t(mph))) {
+                            atomicExch(p.err, 1);
+                            abort_run = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t st = smem_u32(ring + ms * kStageBytes);
+                        const uint64_t ad = smem_desc(st, 128u, 256u);
+                        const uint64_t bd = smem_desc(st + kABytes, 128u, 256u);
+                        mma_f8f6f4(tmem + uint32_t(b * 256), ad, bd, idesc, kb > 0 ? 1u : 0u);
+                        mma_commit(&empty[ms]);  // frees the stage when this MMA completes
+                        if (++ms == kStages) {
+                            ms = 0;
+                            mph ^= 1;
+                        }
+                    }
+                    if (abort_run) break;
+                    mma_commit(&tfull[b]);
+                }
+            }
+            __syncwarp();
+        } else {
+            // -------------------------------------------------- epilogue
+            abort_run = __any_sync(0xffffffffu, abort_run);
+            const float jpf = float(a.jperp_min + lvl * a.jperp_step);
+            const uint32_t JP2 = h2u(__floats2half2_rn(jpf, jpf));
+            const float i0f = float(i0cur);
+            const uint32_t LO2 = h2u(__floats2half2_rn(p.bias - i0f, p.bias - i0f));
+            const uint32_t HI2 = h2u(__floats2half2_rn(p.bias + i0f - float(a.alpha), p.bias + i0f - float(a.alpha)));
+            const uint32_t TOP2 = h2u(__floats2half2_rn(p.bias + i0f, p.bias + i0f));
+            const uint8_t *Aold = Ag + slot_of(t - a.delay, p.L) * p.KB * kABytes;
+            uint8_t *Anext = Ag + slot_of(t + 1, p.L) * p.KB * kABytes;
+            long long esum = 0;
+            for (int m = 0; m < nmine && !abort_run; ++m) {
+                const int ch = rank + m * p.CS;
+                const int b = m & 1;
+                // This thread's words of the chunk: 8 ch + 2 part + {0, 4, 1, 5}.
+                // Words 8 ch + 2 part and + 4 share one Philox call (same counter),
+                // as do + 1 and + 5; both calls are made before the MMAs are awaited.
+                // Output word of word w is (w / 4) % 4 = (2 ch + (q & 1)) % 4.
+                const int wbase = 8 * ch + 2 * part;
+                uint32_t nq0 = 0, nq1 = 0, nq2 = 0, nq3 = 0;
+                if (update) {
+                    const Philox4 ph0 = philox4x32_10(noise_ctr(uint32_t(wbase)), uint32_t(k), trial_g, uint32_t(t),
+                                                      uint32_t(a.seed), uint32_t(a.seed >> 32));
+                    const Philox4 ph1 = philox4x32_10(noise_ctr(uint32_t(wbase + 1)), uint32_t(k), trial_g,
+                                                      uint32_t(t), uint32_t(a.seed), uint32_t(a.seed >> 32));
+                    const bool odd = ch & 1;
+                    nq0 = odd ? ph0.x[2] : ph0.x[0];
+                    nq1 = odd ? ph0.x[3] : ph0.x[1];
+                    nq2 = odd ? ph1.x[2] : ph1.x[0];
+                    nq3 = odd ? ph1.x[3] : ph1.x[1];
+                }
+                const bool ok = mbar_wait(&tfull[b], (et_ph >> b) & 1u);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    if (lane == 0) atomicExch(p.err, 1);
+                    abort_run = true;
+                    break;
+                }
+                et_ph ^= 1u << b;
+                tc_fence_after();
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {
+                    const int w = wbase + 4 * (q & 1) + (q >> 1);
+                    const uint32_t nw = q == 0 ? nq0 : (q == 1 ? nq1 : (q == 2 ? nq2 : nq3));
+#pragma unroll 1
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int i0 = 32 * w + 16 * hh;
+                        if (i0 >= p.N16) continue;  // warp-uniform
+                        uint32_t f[16];
+                        __syncwarp();
+                        tmem_ld16_issue(tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * 256 + (i0 - 256 * ch)), f);
+                        tmem_ld_wait(f);
+                        if (!valid) continue;
+                        const int kb = i0 >> 5;
+                        const uint32_t ob = blk_off(c, i0 & 31);
+                        if (energy) {
+                            // sigma_i (D_i + h_i / jm) = sigma_i (sum_j J_ij sigma_j + 2 h_i) / jm; a
+                            // 16-spin partial sum is an exact float (|terms| <= 2^15)
+                            const uint4 so = *reinterpret_cast<const uint4 *>(Acur + int64_t(kb) * kABytes + ob);
+                            const uint32_t sw[4] = {so.x, so.y, so.z, so.w};
+                            float tsum = 0.f;
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int i = i0 + e;
+                                if (i >= a.N) break;
+                                const float y = __uint_as_float(f[e]) + __ldg(&p.hf[i]);
+                                const uint32_t sgn = (sw[e >> 2] << (24 - 8 * (e & 3))) & 0x80000000u;
+                                tsum += __uint_as_float(__float_as_uint(y) ^ sgn);
+                            }
+                            esum += static_cast<long long>(tsum);
+                            if (!update) continue;
+                        }
+                        // ring neighbours' sigma(t - d) (FP8 bytes, sign bit 7)
+                        const uint4 nu = *reinterpret_cast<const uint4 *>(Aold + int64_t(kb) * kABytes +
+                                                                          blk_off(nb_up, i0 & 31));
+                        const uint32_t nuw[4] = {nu.x, nu.y, nu.z, nu.w};
+                        uint32_t ndw[4] = {0, 0, 0, 0};
+                        if (a.both) {
+                            const uint4 nd = *reinterpret_cast<const uint4 *>(Aold + int64_t(kb) * kABytes +
+                                                                              blk_off(nb_dn, i0 & 31));
+                            ndw[0] = nd.x;
+                            ndw[1] = nd.y;
+                            ndw[2] = nd.z;
+                            ndw[3] = nd.w;
+                        }
+                        const uint4 isv = *reinterpret_cast<const uint4 *>(p.IsB + gcol * a.Np + i0);
+                        const uint32_t isw[4] = {isv.x, isv.y, isv.z, isv.w};
+                        uint32_t isn[8];
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            const int j = hh * 8 + qq;
+                            const uint32_t x2 = pack_h2(f[2 * qq], f[2 * qq + 1]);
+                            const uint32_t n2 = ((nw << j) & kSignPair) ^ p.NR2;
+                            // bytes 2qq, 2qq+1 of the neighbour row: signs to bits 15 / 31
+                            const uint32_t sel = (qq & 1) ? 0x3727 : 0x1707;
+                            const uint32_t c2 = (__byte_perm(nuw[qq >> 1], 0, sel) & kSignPair) ^ JP2;
+                            __half2 y = __hfma2(u2h(x2), u2h(p.JM2), u2h(n2));
+                            y = __hadd2(y, u2h(c2));
+                            if (a.both)
+                                y = __hadd2(y, u2h((__byte_perm(ndw[qq >> 1], 0, sel) & kSignPair) ^ JP2));
+                            const uint32_t ib = __byte_perm(isw[qq >> 1], 0x64646464u, (qq & 1) ? 0x4342 : 0x4140);
+                            const __half2 v = __hadd2(u2h(ib), y);
+                            const __half2 mm = __hmax2(v, u2h(LO2));
+                            const uint32_t ge = __hge2_mask(v, u2h(TOP2));
+                            isn[qq] = (ge & HI2) | (~ge & h2u(mm));
+                        }
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int mq = 0; mq < 4; ++mq) pk[mq] = __byte_perm(isn[2 * mq], isn[2 * mq + 1], 0x6420);
+                        *reinterpret_cast<uint4 *>(p.IsB + gcol * a.Np + i0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        uint4 bo;
+                        bo.x = (~pk[0] & 0x80808080u) | 0x38383838u;
+                        bo.y = (~pk[1] & 0x80808080u) | 0x38383838u;
+                        bo.z = (~pk[2] & 0x80808080u) | 0x38383838u;
+                        bo.w = (~pk[3] & 0x80808080u) | 0x38383838u;
+                        if (i0 + 16 > a.N) bo = mask_tail(bo, i0, a.N);
+                        *reinterpret_cast<uint4 *>(Anext + int64_t(kb) * kABytes + ob) = bo;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+            }
+            if (energy && valid && !abort_run)
+                atomicAdd(&p.eacc[(it & 1) * cols + gcol], static_cast<unsigned long long>(esum));
+            fence_async_global();
+        }
+        // ------------------------------------------------------ cycle end
+        cluster_sync();
+        if (energy && rank == 0 && valid && part == 0) {
+            const long long s = static_cast<long long>(atomicExch(&p.eacc[(it & 1) * cols + gcol], 0ull));
+            const int64_t E = -(int64_t(p.jm) * s) / 2;
+            if (kTrack && it > 0 && E < e_best) {
+                e_best = E;
+                best_cycle = int32_t(t);
+            }
+            if (!update && p.efin) p.efin[gcol] = E;
+        }
+        if (++sub == a.tau) {
+            sub = 0;
+            if (++lvl > a.beta) lvl = 0;
+        }
+        if (++isub == p.i0_tau) {
+            isub = 0;
+            if (++ilvl == p.i0_levels) {
+                ilvl = 0;
+                i0cur = a.I0;
+            } else {
+                i0cur *= p.i0_mult;
+            }
+        }
+    }
+    if (kTrack && rank == 0 && valid && part == 0) {
+        p.ebest[gcol] = e_best;
+        p.bcyc[gcol] = best_cycle;
+    }
+    // Drain before exit: the producer waits (bounded) for its last copy into
+    // every stage, the MMA thread for all MMAs it issued.
+    if (warp == 0 && lane == 0) {
+        for (int s = 0; s < kStages && uint32_t(s) < nis; ++s) {
+            const uint32_t last = (nis - 1u - uint32_t(s)) / uint32_t(kStages);
+            mbar_wait(&full[s], last & 1u);
+        }
+    }
+    if (warp == 1 && lane == 0) {
+        mma_commit(drain);
+        mbar_wait(drain, 0u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    cluster_sync();
+}
+
+// Initial operand slots and counters: sigma(t0 - l) for l = 0..d, the h
+// weight columns in every slot, zero elsewhere; counters Is + 128.
+__global__ void tcs_init_kernel(SParams p, const uint8_t *a_w, int nh) {
+    const AnnealArgs &a = p.a;
+    const int64_t groups = (int64_t(a.trials) + p.Tb - 1) / p.Tb;
+    const int64_t per_slot = int64_t(p.KB) * kABytes;
+    const int64_t total = groups * p.L * per_slot;
+    const int64_t t0 = a.start_cycle;
+    for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < total; x += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t g = x / (p.L * per_slot);
+        const int64_t rem = x % (p.L * per_slot);
+        const int s = int(rem / per_slot);
+        const int64_t inb = rem % per_slot;
+        const int kb = int(inb / kABytes);
+        const int off = int(inb % kABytes);
+        // invert blk_off: off = (r/8)*256 + kc*128 + (r%8)*16 + e
+        const int r = (off >> 8) * 8 + ((off >> 4) & 7);
+        const int kk = kb * 32 + ((off >> 7) & 1) * 16 + (off & 15);
+        const int64_t trial = g * p.Tb + r / a.R;
+        const bool vr = r < p.Tb * a.R && trial < a.trials;
+        uint8_t v = 0;
+        if (vr) {
+            const int kr = r % a.R;
+            const int64_t col = trial * a.R + kr;
+            if (kk >= p.N16 && kk < p.N16 + nh) {
+                v = a_w[kk - p.N16];
+            } else if (kk < a.N) {
+                // which history level is slot s?  level l with slot(t0 - l) == s
+                int lev = -1;
+                for (int l = 0; l <= a.delay; ++l)
+                    if (slot_of(t0 - l, p.L) == s) lev = l;
+                if (lev >= 0) {
+                    int8_t sg;
+                    if (a.init_mode == SSQA_INIT_FROM_STATE) {
+                        sg = lev == 0 ? a.sigma[col * a.N + kk]
+                                      : a.hist[((trial * a.delay + (lev - 1)) * a.R + kr) * int64_t(a.N) + kk];
+                    } else if (a.init_mode == SSQA_INIT_RANDOM) {
+                        const uint32_t w = noise_word(a.seed, uint32_t(kk), uint32_t(kr), a.trial_offset + uint32_t(trial),
+                                                      0xFFFFFFFFu);
+                        sg = ((w >> spin_bit_pos(uint32_t(kk))) & 1u) ? int8_t(-1) : int8_t(1);
+                    } else {
+                        sg = -1;
+                    }
+                    v = sg < 0 ? 0xB8 : 0x38;
+                }
+            }
+        }
+        p.A[x] = v;
+    }
+    const int64_t cols = int64_t(a.trials) * a.R;
+    for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < cols * a.Np;
+         x += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t col = x / a.Np;
+        const int i = int(x % a.Np);
+        int v = 0;
+        if (i < a.N && a.init_mode == SSQA_INIT_FROM_STATE) v = a.Is[col * a.N + i];
+        if (v < -128 || v > 127) {
+            atomicExch(p.err, 2);  // the byte counters cannot hold this state
+            v = 0;
+        }
+        p.IsB[x] = uint8_t(v + 128);
+    }
+    for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < 2 * cols; x += int64_t(gridDim.x) * blockDim.x)
+        p.eacc[x] = 0ull;
+}
+
+// Results: sigma(tf), history, counters (the energies are written by the kernel).
+__global__ void tcs_finish_kernel(SParams p, int64_t tf) {
+    const AnnealArgs &a = p.a;
+    const int64_t cols = int64_t(a.trials) * a.R;
+    for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < cols * a.N; x += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t col = x / a.N;
+        const int i = int(x % a.N);
+        const int64_t trial = col / a.R;
+        const int kr = int(col % a.R);
+        const int64_t g = trial / p.Tb;
+        const int r = int((trial % p.Tb) * a.R + kr);
+        const uint8_t *Ag = p.A + g * int64_t(p.L) * p.KB * kABytes;
+        const int64_t o = int64_t(i >> 5) * kABytes + blk_off(r, i & 31);
+        a.sigma[x] = (Ag[slot_of(tf, p.L) * p.KB * kABytes + o] & 0x80) ? int8_t(-1) : int8_t(1);
+        if (a.hist)
+            for (int l = 0; l < a.delay; ++l)
+                a.hist[((trial * a.delay + l) * a.R + kr) * int64_t(a.N) + i] =
+                    (Ag[slot_of(tf - 1 - l, p.L) * p.KB * kABytes + o] & 0x80) ? int8_t(-1) : int8_t(1);
+        a.Is[x] = int32_t(p.IsB[col * a.Np + i]) - 128;
+    }
+}
+
+inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+void configure_once(void (*fn)(SParams), int smem) {
+    static std::mutex mu;
+    static std::set<std::pair<int, void (*)(SParams)>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, fn})) return;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared));
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin > smem ? optin : smem);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    done.insert({dev, fn});
+}
+
+}  // namespace tcs
+
+bool tcs_supported(const TcImage &img, const AnnealArgs &a, std::string *why) {
+    if (!img.s_ok) {
+        *why = img.why.empty() ? "no streamed operand image (N <= 256 or too many h digits)" : img.why;
+        return false;
+    }
+    if (img.nh > 16) {
+        *why = "too many h digit columns";
+        return false;
+    }
+    if (a.R > 128) {
+        *why = "R > 128";
+        return false;
+    }
+    const int64_t jpmax = std::max<int64_t>(std::llabs(int64_t(a.jperp_min)),
+                                            std::llabs(int64_t(a.jperp_min) + int64_t(a.jperp_step) * a.beta));
+    const int64_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
+    if (i0_top > 127) {
+        *why = "counters above 127 do not fit the byte state of the streamed path";
+        return false;
+    }
+    if (i0_top + a.n_rnd + (a.both ? 2 : 1) * jpmax > 1024) {
+        *why = "I0 + n_rnd + |J_perp| terms exceed the exact FP16 epilogue range (1024)";
+        return false;
+    }
+    return true;
+}
+
+size_t tcs_scratch_bytes(const TcImage &img, const AnnealArgs &a) {
+    const int64_t Tb = 128 / a.R;
+    const int64_t groups = (int64_t(a.trials) + Tb - 1) / Tb;
+    const int64_t cols = int64_t(a.trials) * a.R;
+    const int L = a.delay + 2;
+    return tcs::up256(size_t(groups) * L * img.KB * tcs::kABytes) + tcs::up256(size_t(cols) * a.Np) +
+           tcs::up256(size_t(cols) * 16) + tcs::up256(size_t(cols) * 8) + tcs::up256(sizeof(int));
+}
+
+int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *scratch, void *stream) {
+    using namespace tcs;
+    std::string why;
+    if (!tcs_supported(img, a, &why)) return fail(SSQA_ERR_UNSUPPORTED, "streamed tensor path: " + why);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.a = a;
+    p.B = dc.tcs_b;
+    p.hf = dc.tcs_hf;
+    p.N16 = img.N16;
+    p.KB = img.KB;
+    p.NCH = img.NCH;
+    p.last_rows = img.N16 - 256 * (img.NCH - 1);
+    p.L = a.delay + 2;
+    p.Tb = 128 / a.R;
+    p.jm = img.jm;
+    p.NR2 = 0;
+    {
+        const __half2 h = __floats2half2_rn(float(a.n_rnd), float(a.n_rnd));
+        std::memcpy(&p.NR2, &h, 4);
+        const __half2 j = __floats2half2_rn(float(img.jm), float(img.jm));
+        std::memcpy(&p.JM2, &j, 4);
+    }
+    p.bias = 1152.f;
+    p.i0_levels = 1;
+    p.i0_mult = 2;
+    p.i0_tau = 1 << 30;
+    if (a.i0_max > a.I0) {
+        for (int64_t v = a.I0; v < a.i0_max; v *= a.i0_mult) ++p.i0_levels;
+        p.i0_mult = a.i0_mult;
+        p.i0_tau = a.i0_tau;
+    }
+    const int64_t groups = (int64_t(a.trials) + p.Tb - 1) / p.Tb;
+    const int64_t cols = int64_t(a.trials) * a.R;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int CS = int(nsm / (groups > 0 ? groups : 1));
+    if (CS > 8) CS = 8;
+    if (CS > p.NCH) CS = p.NCH;
+    if (CS < 1) CS = 1;
+    uint8_t *q = static_cast<uint8_t *>(scratch);
+    p.A = q;
+    q += up256(size_t(groups) * p.L * p.KB * kABytes);
+    p.IsB = q;
+    q += up256(size_t(cols) * a.Np);
+    p.eacc = reinterpret_cast<unsigned long long *>(q);
+    q += up256(size_t(cols) * 16);
+    p.efin = a.e_final;
+    p.ebest = a.e_best;
+    p.bcyc = a.best_cycle;
+    q += up256(size_t(cols) * 8);
+    p.err = reinterpret_cast<int *>(q);
+    uint8_t *aw = nullptr;
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&aw), 16, st);
+    if (e) return fail(SSQA_ERR_OOM, std::string("streamed tensor path: ") + cudaGetErrorString(e));
+    if (img.nh) cudaMemcpyAsync(aw, img.a_w.data(), img.nh, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(p.err, 0, sizeof(int), st);
+    tcs_init_kernel<<<2048, 256, 0, st>>>(p, aw, img.nh);
+    if (a.init_mode == SSQA_INIT_FROM_STATE) {
+        int herr = 0;
+        e = cudaMemcpyAsync(&herr, p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaStreamSynchronize(st);
+        if (!e && herr == 2) {
+            cudaFreeAsync(aw, st);
+            return fail(SSQA_ERR_UNSUPPORTED, "streamed tensor path: resumed counters outside -128..127");
+        }
+    }
+    void (*fn)(SParams) = a.track_best ? ssqa_tcs_kernel<true> : ssqa_tcs_kernel<false>;
+    const int smem = kStages * kStageBytes + 1024 + 512;  // ring + alignment + barriers
+    configure_once(fn, smem);
+    cudaLaunchConfig_t cfg{};
+    cfg.blockDim = dim3(kThr, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // the largest cluster (<= CS) that the device can place at least once
+    for (; CS > 1; --CS) {
+        int nclus = 0;
+        cfg.gridDim = dim3(unsigned(groups * CS), 1, 1);
+        attr[0].val.clusterDim.x = unsigned(CS);
+        if (cudaOccupancyMaxActiveClusters(&nclus, fn, &cfg) == cudaSuccess && nclus > 0) break;
+        cudaGetLastError();
+    }
+    p.CS = CS;
+    cfg.gridDim = dim3(unsigned(groups * CS), 1, 1);
+    attr[0].val.clusterDim.x = unsigned(CS);
+    if (!e) e = cudaLaunchKernelEx(&cfg, fn, p);
+    if (!e) {
+        tcs_finish_kernel<<<2048, 256, 0, st>>>(p, int64_t(a.start_cycle) + a.cycles);
+        e = cudaGetLastError();
+    }
+    int herr = 0;
+    if (!e) e = cudaMemcpyAsync(&herr, p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(aw, st);
+    if (e) return fail(SSQA_ERR_DEVICE, std::string("streamed tensor path kernel: ") + cudaGetErrorString(e));
+    if (herr) return fail(SSQA_ERR_TIMEOUT, "streamed tensor path: a bounded wait timed out");
+    return SSQA_OK;
+}
+
+}  // namespace ssqa
