@@ -45,7 +45,7 @@ constexpr int kMaxG = 8;                 // 16-spin granules per epilogue thread
 constexpr int kMaxW = 4;                 // 32-spin words per epilogue thread
 constexpr uint32_t kSignPair = 0x80008000u;
 constexpr int kMaxNh = 16;
-constexpr long long kWaitNs = 4000000000LL;  // bounded waits: 4 s
+constexpr long long kWaitCycles = 8000000000LL;  // bounded waits: 8e9 SM clocks (about 4 s)
 
 struct TcParams {
     AnnealArgs a;
@@ -67,11 +67,6 @@ struct TcParams {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ long long global_ns() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -86,12 +81,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for phase `parity` of an mbarrier; false after kWaitNs.
+// Wait for phase `parity` of an mbarrier; false after kWaitCycles.  The bound
+// uses the SM clock counter: reading it costs no more than an ALU op, where a
+// global-timer read on every poll slowed pipelines that wait once per stage.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = global_ns();
+    const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
     return true;
 }
 __device__ __forceinline__ void fence_mbar_init() {
@@ -221,7 +218,10 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
 
     const AnnealArgs &a = p.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool mma_warp = warp == 0;  // allocates TMEM; lane 0 issues the MMAs
+    // The last warp allocates TMEM and (lane 0) issues the MMAs.  Issue blocks
+    // while the tensor cores work, so the issuing warp starts its epilogue late:
+    // it is the warp of the last part, which owns the fewest spin words.
+    const bool mma_warp = warp == kEpiWarps - 1;
     const int Kp = p.Kp;
     const int64_t trial0 = int64_t(blockIdx.x) * p.Tb;
     const int ntr = int(a.trials - trial0 < p.Tb ? a.trials - trial0 : p.Tb);
