@@ -163,3 +163,31 @@ def test_sk_n8192_full_trials():
     o = O.anneal(h, J, R=c["R"], cycles=3, trials=1, seed=c["seed"], tau=c["tau"], trial_offset=c["trials"] - 1)
     for k in ("sigma", "Is", "E_final"):
         np.testing.assert_array_equal(g[k][-1:], o[k], err_msg=k)
+
+
+@pytest.mark.parametrize("case", ["dummy_steps", "padded_groups"])
+def test_streamed_cluster_shapes(case):
+    # On a 152-SM device: N = 1100 has 5 chunks over 4 ranks (ranks with fewer
+    # chunks run dummy steps); 17 groups of R = 32 columns pad to 18 for 2-group
+    # clusters.  All trials equal the delta path; sampled trials equal the oracle.
+    if case == "dummy_steps":
+        I = sk(1100, 7, hscale=12)
+        kw = dict(R=16, cycles=20, trials=256, seed=81, tau=4, delay=2)
+        sample = (0, 255)
+    else:
+        I = gi(45, 0.5, 45, 46)
+        kw = dict(R=32, cycles=15, trials=65, seed=82, tau=3, coupling=1)
+        sample = (64,)
+    g = S.anneal(I, algo=ST, track_best=True, **kw)
+    de = S.anneal(I, algo=S.ALGO_DELTA, track_best=True, **kw)
+    for k in ("sigma", "Is", "E_final", "E_best", "best_cycle"):
+        np.testing.assert_array_equal(g[k], de[k], err_msg=k)
+    h, J, _ = I.export()
+    okw = dict(kw)
+    if "coupling" in okw:
+        okw["coupling_both"] = okw.pop("coupling")
+    okw["trials"] = 1
+    for tr in sample:
+        o = O.anneal(h, J, trial_offset=tr, track_best=True, **okw)
+        for k in ("sigma", "Is", "E_final", "E_best", "best_cycle"):
+            np.testing.assert_array_equal(g[k][tr:tr + 1], o[k], err_msg=k)
