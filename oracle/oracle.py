@@ -80,7 +80,7 @@ def lib():
             L.or_tts.argtypes = [ctypes.c_double] * 3
             L.or_tts.restype = ctypes.c_double
             L.or_anneal.argtypes = [ctypes.POINTER(Params), i64p, i64p, ctypes.c_int32, ctypes.c_uint32,
-                                    i8p, i8p, i32p, i64p, i64p, i32p]
+                                    i8p, i8p, i32p, i64p, i64p, i32p, i64p]
             L.or_ssa_i0.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
             L.or_ssa_i0.restype = ctypes.c_int32
             L.or_ssa_trial.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -211,11 +211,12 @@ PAPER_DEFAULTS = dict(I0=24, alpha=1, n_rnd=12, jperp_min=0, jperp_max=6, beta=3
 
 
 def anneal(h, J, *, R: int, cycles: int, trials: int, seed: int, trial_offset: int = 0,
-           track_best: bool = False, state=None, **kw):
+           track_best: bool = False, state=None, trace: bool = False, **kw):
     """Run Eq. 6 for `trials` trials; returns a dict of numpy arrays.
 
     state: optional dict(sigma [T,R,N] int8, hist [T,d,R,N] int8, Is [T,R,N] int32)
-    used with init_mode=2 (resume)."""
+    used with init_mode=2 (resume).  trace: also return E_trace [cycles,T,R],
+    the energy of every replica after every cycle (Fig. 6)."""
     h = np.ascontiguousarray(h, dtype=np.int64)
     J = np.ascontiguousarray(J, dtype=np.int64)
     N = h.shape[0]
@@ -234,12 +235,15 @@ def anneal(h, J, *, R: int, cycles: int, trials: int, seed: int, trial_offset: i
     E_final = np.zeros((trials, R), dtype=np.int64)
     E_best = np.zeros((trials, R), dtype=np.int64) if track_best else None
     best_cycle = np.zeros((trials, R), dtype=np.int32) if track_best else None
+    E_trace = np.zeros((cycles, trials, R), dtype=np.int64) if trace else None
     rc = lib().or_anneal(ctypes.byref(p), _p(h), _p(J), trials, trial_offset, _p(sigma),
-                         _p(hist), _p(Is), _p(E_final), _p(E_best), _p(best_cycle))
+                         _p(hist), _p(Is), _p(E_final), _p(E_best), _p(best_cycle), _p(E_trace))
     _check(rc, "anneal")
     out = dict(sigma=sigma, hist=hist, Is=Is, E_final=E_final)
     if track_best:
         out.update(E_best=E_best, best_cycle=best_cycle)
+    if trace:
+        out["E_trace"] = E_trace
     return out
 
 

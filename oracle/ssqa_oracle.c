@@ -373,10 +373,13 @@ typedef struct {
 /* One trial.  J, h: scaled integers (J zero diagonal, symmetric).
  * State arrays are [R][N].  hist is [delay][R][N]: hist[l] = sigma(t0-1-l);
  * read when init_mode == 2, written at the end.  E_best/best_cycle track the
- * energy of sigma(t) for t = t0+1 .. t0+cycles (first cycle reaching it). */
+ * energy of sigma(t) for t = t0+1 .. t0+cycles (first cycle reaching it).
+ * E_trace (optional) receives that energy every cycle, the waveform of Fig. 6:
+ * E_trace[c * trace_stride + k] = E(sigma_k(t0 + c + 1)). */
 int or_anneal_trial(const or_params *p, const int64_t *h, const int64_t *J,
                     uint32_t trial, int8_t *sigma, int8_t *hist, int32_t *Is,
-                    int64_t *E_final, int64_t *E_best, int32_t *best_cycle)
+                    int64_t *E_final, int64_t *E_best, int32_t *best_cycle,
+                    int64_t *E_trace, int64_t trace_stride)
 {
     int N = p->N, R = p->R, d = p->delay;
     int L = d + 1; /* levels kept: sigma(t), sigma(t-1), ..., sigma(t-d) */
@@ -455,7 +458,7 @@ int or_anneal_trial(const or_params *p, const int64_t *h, const int64_t *J,
         memmove(ring + (size_t)R * N, ring, (size_t)(L - 1) * R * N);
         memcpy(ring, next, (size_t)R * N);
         memcpy(Is, Is_next, sizeof(int32_t) * (size_t)R * N);
-        if (E_best)
+        if (E_best || E_trace)
             for (k = 0; k < R; ++k) {
                 int8_t *s = ring + (size_t)k * N;
                 int64_t E = 0;
@@ -464,10 +467,12 @@ int or_anneal_trial(const or_params *p, const int64_t *h, const int64_t *J,
                     for (j = i + 1; j < N; ++j)
                         E -= J[(size_t)i * N + j] * s[i] * s[j];
                 }
-                if (E < E_best[k]) {
+                if (E_best && E < E_best[k]) {
                     E_best[k] = E;
                     best_cycle[k] = (int32_t)(t + 1);
                 }
+                if (E_trace)
+                    E_trace[c * trace_stride + k] = E;
             }
     }
     memcpy(sigma, ring, (size_t)R * N);
@@ -483,10 +488,12 @@ int or_anneal_trial(const or_params *p, const int64_t *h, const int64_t *J,
 
 /* All trials: trial indices trial_offset .. trial_offset + trials - 1.
  * Arrays are [trials][R][N] (hist [trials][delay][R][N]); E arrays
- * [trials][R].  Optional arrays may be NULL (E_best with best_cycle). */
+ * [trials][R]; E_trace [cycles][trials][R].  Optional arrays may be NULL
+ * (E_best with best_cycle). */
 int or_anneal(const or_params *p, const int64_t *h, const int64_t *J,
               int32_t trials, uint32_t trial_offset, int8_t *sigma, int8_t *hist,
-              int32_t *Is, int64_t *E_final, int64_t *E_best, int32_t *best_cycle)
+              int32_t *Is, int64_t *E_final, int64_t *E_best, int32_t *best_cycle,
+              int64_t *E_trace)
 {
     size_t RN = (size_t)p->R * p->N;
     int32_t tr;
@@ -496,7 +503,8 @@ int or_anneal(const or_params *p, const int64_t *h, const int64_t *J,
             hist ? hist + (size_t)tr * p->delay * RN : NULL, Is + tr * RN,
             E_final ? E_final + (size_t)tr * p->R : NULL,
             E_best ? E_best + (size_t)tr * p->R : NULL,
-            E_best ? best_cycle + (size_t)tr * p->R : NULL);
+            E_best ? best_cycle + (size_t)tr * p->R : NULL,
+            E_trace ? E_trace + (size_t)tr * p->R : NULL, (int64_t)trials * p->R);
         if (rc)
             return rc;
     }

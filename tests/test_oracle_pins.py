@@ -424,3 +424,21 @@ def test_ssa_schedule_is_ssqa_r1_with_i0_schedule():
     # the schedule matters: a fixed I0 gives a different trajectory
     f = O.anneal(h, J, R=1, cycles=230, trials=1, seed=43, trial_offset=2, jperp_max=0, I0=4, alpha=1, n_rnd=4)
     assert not np.array_equal(f["Is"], q["Is"])
+
+
+def test_energy_trace_matches_best_final_and_shorter_runs():
+    """E_trace[c] = E(sigma(t0 + c + 1)) (Fig. 6): its minimum and first argmin
+    are E_best / best_cycle, its last row is E_final, and row c equals the final
+    energy of a straight run of c + 1 cycles (same seeds)."""
+    h, J, off = _gi()
+    kw = dict(R=3, trials=2, seed=73, tau=2, trial_offset=5)
+    full = O.anneal(h, J, cycles=17, track_best=True, trace=True, **kw)
+    tr = full["E_trace"]
+    assert tr.shape == (17, 2, 3)
+    np.testing.assert_array_equal(tr.min(axis=0), full["E_best"])
+    np.testing.assert_array_equal(tr.argmin(axis=0) + 1, full["best_cycle"])
+    np.testing.assert_array_equal(tr[-1], full["E_final"])
+    for c in (0, 4, 11):
+        short = O.anneal(h, J, cycles=c + 1, **kw)
+        np.testing.assert_array_equal(tr[c], short["E_final"])
+    assert (tr >= -off).all()
