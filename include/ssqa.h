@@ -187,7 +187,11 @@ void ssqa_params_default(ssqa_params *p);
  *              replica; may be NULL.
  *   e_best     [trials][R] int64 and best_cycle [trials][R] int32: lowest
  *              E' over sigma(t0+1 .. t0+cycles) and the first t reaching it;
- *              written with SSQA_FLAG_TRACK_BEST (both non-NULL then). */
+ *              written with SSQA_FLAG_TRACK_BEST (both non-NULL then).
+ *   e_trace    [cycles][trials][R] int64: E'(sigma(t0 + c + 1)) of every
+ *              replica after every cycle c, the energy waveform of Fig. 6
+ *              (Sec. 4.3); may be NULL; needs SSQA_FLAG_TRACK_BEST (the same
+ *              per-cycle energies).  Not returned by ssqa_poll (serving). */
 typedef struct ssqa_result {
     int8_t *sigma;
     int8_t *sigma_hist;
@@ -195,6 +199,7 @@ typedef struct ssqa_result {
     int64_t *e_final;
     int64_t *e_best;
     int32_t *best_cycle;
+    int64_t *e_trace;
 } ssqa_result;
 
 /* Run SSQA (Eq. 6a-6c, Sec. 3.2) on all N*R spins of every trial in

@@ -45,6 +45,7 @@ class Result(ctypes.Structure):
     _fields_ = [
         ("sigma", ctypes.c_void_p), ("sigma_hist", ctypes.c_void_p), ("is_state", ctypes.c_void_p),
         ("e_final", ctypes.c_void_p), ("e_best", ctypes.c_void_p), ("best_cycle", ctypes.c_void_p),
+        ("e_trace", ctypes.c_void_p),
     ]
 
 
@@ -183,8 +184,11 @@ def make_params(*, R: int, cycles: int, trials: int, seed: int, **kw) -> Params:
 
 
 def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_best: bool = False,
-           state=None, want_hist: bool = False, stream=None, **kw):
-    """Anneal with host buffers; returns numpy arrays (sigma, Is, E_final, ...)."""
+           state=None, want_hist: bool = False, want_trace: bool = False, stream=None, **kw):
+    """Anneal with host buffers; returns numpy arrays (sigma, Is, E_final, ...).
+    want_trace (implies track_best): E_trace [cycles, trials, R], the energy of
+    every replica after every cycle."""
+    track_best = track_best or want_trace
     N = ising.N
     p = make_params(R=R, cycles=cycles, trials=trials, seed=seed, **kw)
     if track_best:
@@ -201,7 +205,8 @@ def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_b
     E = np.zeros((trials, R), np.int64)
     Eb = np.zeros((trials, R), np.int64) if track_best else None
     bc = np.zeros((trials, R), np.int32) if track_best else None
-    r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(E), _ptr(Eb), _ptr(bc))
+    tr = np.zeros((cycles, trials, R), np.int64) if want_trace else None
+    r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(E), _ptr(Eb), _ptr(bc), _ptr(tr))
     st = None if stream is None else ctypes.c_void_p(int(stream))
     _check(lib().ssqa_anneal(ising.handle, ctypes.byref(p), ctypes.byref(r), st), "anneal")
     out = dict(sigma=sigma, Is=Is, E_final=E)
@@ -209,11 +214,13 @@ def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_b
         out["hist"] = hist
     if track_best:
         out.update(E_best=Eb, best_cycle=bc)
+    if want_trace:
+        out["E_trace"] = tr
     return out
 
 
 def anneal_device(ising: Ising, params: Params, sigma, Is, e_final=None, hist=None, e_best=None, best_cycle=None,
-                  stream=None):
+                  stream=None, e_trace=None):
     """Anneal on device buffers (torch CUDA tensors); enqueued on `stream`
     (a torch.cuda.Stream or raw handle, default: torch's current stream)."""
     import torch
@@ -225,7 +232,7 @@ def anneal_device(ising: Ising, params: Params, sigma, Is, e_final=None, hist=No
     if stream is None:
         stream = torch.cuda.current_stream()
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(e_final), _ptr(e_best), _ptr(best_cycle))
+    r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(e_final), _ptr(e_best), _ptr(best_cycle), _ptr(e_trace))
     _check(lib().ssqa_anneal(ising.handle, ctypes.byref(p), ctypes.byref(r), ctypes.c_void_p(handle)), "anneal")
 
 

@@ -82,6 +82,29 @@ def cmd_serve(args):
     print(_json.dumps(out), flush=True)
 
 
+def cmd_sweep(args):
+    import json
+
+    import torch
+
+    import paper_2302_12454_gb300 as S
+    from paper_2302_12454_gb300 import build as B
+    from paper_2302_12454_gb300 import sweep as SW
+    from paper_2302_12454_gb300 import workloads as W
+
+    B.build()
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    if args.table == 4:
+        sizes = tuple(int(x) for x in args.sizes.split(",")) if args.sizes else SW.TABLE4_N
+        rows = SW.table4(S, W, torch, sizes=sizes, trials=args.trials, with_ssa=not args.no_ssa,
+                         ssqa_alpha=args.ssqa_alpha, ssa_alpha=args.ssa_alpha, log=log)
+    else:
+        sizes = tuple(int(x) for x in args.sizes.split(",")) if args.sizes else SW.TABLE3_N
+        rows = SW.table3(S, W, torch, sizes=sizes, trials=args.trials, alpha=args.ssqa_alpha, log=log)
+    for r in rows:
+        print(json.dumps(r), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2302_12454_gb300")
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -100,11 +123,20 @@ def main(argv=None):
     sv.add_argument("--cycles", default="1000,2000,5000")
     sv.add_argument("--slots", type=int, default=32)
     sv.add_argument("--load", type=float, default=0.8)
+    sw = sub.add_parser("sweep", help="P_s / TTS sweep on synthetic GI (Table 4 sizes or Table 3 cases) on cuda:0")
+    sw.add_argument("--table", type=int, default=4, choices=[3, 4])
+    sw.add_argument("--trials", type=int, default=100)
+    sw.add_argument("--sizes", default="", help="comma-separated N (squares of the graph sizes)")
+    sw.add_argument("--no-ssa", action="store_true", help="Table 4 without the SSA arm")
+    sw.add_argument("--ssqa-alpha", type=int, default=1, help="SSQA counter resolution alpha' (scaled units)")
+    sw.add_argument("--ssa-alpha", type=int, default=1, help="SSA counter resolution alpha' (scaled units)")
     args = ap.parse_args(argv)
     if args.cmd == "anneal":
         cmd_anneal(args)
     elif args.cmd == "serve-bench":
         cmd_serve(args)
+    elif args.cmd == "sweep":
+        cmd_sweep(args)
 
 
 if __name__ == "__main__":

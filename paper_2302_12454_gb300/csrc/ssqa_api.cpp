@@ -507,6 +507,8 @@ int validate(const ssqa_ising *I, const ssqa_params *p, const ssqa_result *r) {
         return fail(SSQA_ERR_INVALID_ARG, "resuming with delay > 0 needs sigma_hist");
     if ((p->flags & SSQA_FLAG_TRACK_BEST) && (!r->e_best || !r->best_cycle))
         return fail(SSQA_ERR_INVALID_ARG, "TRACK_BEST needs e_best and best_cycle");
+    if (r->e_trace && !(p->flags & SSQA_FLAG_TRACK_BEST))
+        return fail(SSQA_ERR_INVALID_ARG, "e_trace needs SSQA_FLAG_TRACK_BEST");
     if (p->flags & ~(SSQA_FLAG_TRACK_BEST | SSQA_FLAG_DEVICE_PTRS))
         return fail(SSQA_ERR_INVALID_ARG, "unknown flag bits");
     if (p->i0_max > p->I0) {
@@ -575,7 +577,7 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     a.h = dc->h;
 
     // state / result buffers on the device
-    DevBuf b_sig, b_hist, b_is, b_ef, b_eb, b_bc;
+    DevBuf b_sig, b_hist, b_is, b_ef, b_eb, b_bc, b_tr;
     auto alloc = [&](DevBuf &b, size_t bytes) -> cudaError_t {
         b.s = st;
         return dev_alloc(&b.p, bytes ? bytes : 1, st);
@@ -588,6 +590,7 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
         a.e_final = r->e_final;
         a.e_best = a.track_best ? r->e_best : nullptr;
         a.best_cycle = a.track_best ? r->best_cycle : nullptr;
+        a.e_trace = r->e_trace;
     } else {
         if ((e = alloc(b_sig, nsp))) return cuda_fail(e, "ssqa_anneal: state allocation");
         if ((e = alloc(b_is, nsp * 4))) return cuda_fail(e, "ssqa_anneal: state allocation");
@@ -606,6 +609,10 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
             if ((e = alloc(b_bc, cols * 4))) return cuda_fail(e, "ssqa_anneal: result allocation");
             a.e_best = static_cast<int64_t *>(b_eb.p);
             a.best_cycle = static_cast<int32_t *>(b_bc.p);
+        }
+        if (r->e_trace) {
+            if ((e = alloc(b_tr, size_t(p->cycles) * cols * 8))) return cuda_fail(e, "ssqa_anneal: trace allocation");
+            a.e_trace = static_cast<int64_t *>(b_tr.p);
         }
         if (p->init_mode == SSQA_INIT_FROM_STATE) {
             if ((e = cudaMemcpyAsync(a.sigma, r->sigma, nsp, cudaMemcpyHostToDevice, st)) ||
@@ -660,6 +667,9 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
         if (a.track_best &&
             ((e = cudaMemcpyAsync(r->e_best, a.e_best, cols * 8, cudaMemcpyDeviceToHost, st)) ||
              (e = cudaMemcpyAsync(r->best_cycle, a.best_cycle, cols * 4, cudaMemcpyDeviceToHost, st))))
+            return cuda_fail(e, "ssqa_anneal: result download");
+        if (r->e_trace && p->cycles > 0 &&
+            (e = cudaMemcpyAsync(r->e_trace, a.e_trace, size_t(p->cycles) * cols * 8, cudaMemcpyDeviceToHost, st)))
             return cuda_fail(e, "ssqa_anneal: result download");
         if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "ssqa_anneal");
     }

@@ -237,14 +237,17 @@ __global__ void delta_init_kernel(AnnealArgs a, DeltaState s) {
     }
 }
 
+// E_best / best_cycle update with the energies of sigma(tc); the row of the
+// energy trace for tc, when traced.
 __global__ void delta_best_kernel(int64_t *src, int halve, int64_t *e_best, int32_t *best_cycle, int64_t cols,
-                                  int32_t tc) {
+                                  int32_t tc, int64_t *trace_row) {
     for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < cols; c += int64_t(gridDim.x) * blockDim.x) {
         int64_t E = src[c];
         if (halve) {
             E /= 2;
             src[c] = 0;
         }
+        if (trace_row) trace_row[c] = E;
         if (E < e_best[c]) {
             e_best[c] = E;
             best_cycle[c] = tc;
@@ -393,7 +396,8 @@ int delta_anneal(const AnnealArgs &a, void *scratch, void *stream) {
         if (a.track_best && c > 0) {
             delta_update_kernel<true><<<grid, kSp * kWarps, 0, st>>>(a, s, uint32_t(t), jp, I0, cur, old, nxt, cnt_w,
                                                                      s.total + wp);
-            delta_best_kernel<<<256, 256, 0, st>>>(s.e2acc, 1, a.e_best, a.best_cycle, s.cols, int32_t(t));
+            delta_best_kernel<<<256, 256, 0, st>>>(s.e2acc, 1, a.e_best, a.best_cycle, s.cols, int32_t(t),
+                                                   a.e_trace ? a.e_trace + (c - 1) * s.cols : nullptr);
         } else {
             delta_update_kernel<false><<<grid, kSp * kWarps, 0, st>>>(a, s, uint32_t(t), jp, I0, cur, old, nxt, cnt_w,
                                                                       s.total + wp);
@@ -411,7 +415,8 @@ int delta_anneal(const AnnealArgs &a, void *scratch, void *stream) {
                                    s.efin, stream))
             return rc;
         if (a.track_best && a.cycles > 0) {
-            delta_best_kernel<<<256, 256, 0, st>>>(s.efin, 0, a.e_best, a.best_cycle, s.cols, int32_t(tf));
+            delta_best_kernel<<<256, 256, 0, st>>>(s.efin, 0, a.e_best, a.best_cycle, s.cols, int32_t(tf),
+                                                   a.e_trace ? a.e_trace + (a.cycles - 1) * s.cols : nullptr);
             if (int rc = launch_check("delta best")) return rc;
         }
     }

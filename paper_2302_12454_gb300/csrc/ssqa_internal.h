@@ -101,6 +101,7 @@ struct AnnealArgs {
     int32_t *Is;          // [cols][N]   in/out
     int64_t *e_final;     // [cols] or null
     int64_t *e_best;      // [cols] or null
+    int64_t *e_trace;     // [cycles][cols] or null: E(sigma(t0 + c + 1)), needs track_best
     int32_t *best_cycle;  // [cols] or null
 };
 

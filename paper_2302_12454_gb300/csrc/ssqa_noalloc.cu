@@ -86,6 +86,8 @@ int check_params(int32_t N, const ssqa_params *p, const ssqa_result *r) {
         return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: resuming with delay > 0 needs sigma_hist");
     if ((p->flags & SSQA_FLAG_TRACK_BEST) && (!r->e_best || !r->best_cycle))
         return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: TRACK_BEST needs e_best and best_cycle");
+    if (r->e_trace && !(p->flags & SSQA_FLAG_TRACK_BEST))
+        return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: e_trace needs SSQA_FLAG_TRACK_BEST");
     return SSQA_OK;
 }
 
@@ -128,6 +130,7 @@ extern "C" int ssqa_anneal_noalloc(int32_t N, const int8_t *J_padded, const int3
     a.e_final = out->e_final;
     a.e_best = a.track_best ? out->e_best : nullptr;
     a.best_cycle = a.track_best ? out->best_cycle : nullptr;
+    a.e_trace = a.track_best ? out->e_trace : nullptr;
     const size_t need = ssqa::plain_scratch_bytes(a);
     if (need > kNoallocScratchBytes)
         return ssqa::fail(SSQA_ERR_INVALID_ARG,

@@ -572,6 +572,8 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                         e_best = E;
                         best_cycle = int32_t(t);
                     }
+                    if (kTrack && it > 0 && a.e_trace)
+                        a.e_trace[int64_t(it - 1) * (int64_t(a.trials) * a.R) + col0 + c] = E;
                     if (!update) e_fin = E;
                 }
             }

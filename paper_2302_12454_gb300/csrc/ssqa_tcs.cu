@@ -376,6 +376,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                 e_best = E;
                 best_cycle = int32_t(t);
             }
+            if (kTrack && it > 0 && a.e_trace) a.e_trace[int64_t(it - 1) * cols + gcol] = E;
             if (!update && p.efin) p.efin[gcol] = E;
         }
         if (++sub == a.tau) {

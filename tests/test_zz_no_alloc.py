@@ -46,7 +46,7 @@ def test_noalloc_matches_anneal_twice():
     stream = torch.cuda.current_stream()
     for call in range(2):
         I, kw = cases[call]
-        ref = S.anneal(I, algo=S.ALGO_PLAIN, track_best=True, want_hist=True, **kw)
+        ref = S.anneal(I, algo=S.ALGO_PLAIN, track_best=True, want_hist=True, want_trace=True, **kw)
         Jd, hd, N = _device_inputs(I, torch)
         p = S.make_params(**kw)
         p.flags = S.FLAG_DEVICE_PTRS | S.FLAG_TRACK_BEST
@@ -57,7 +57,9 @@ def test_noalloc_matches_anneal_twice():
         E = torch.zeros((T, R), dtype=torch.int64, device="cuda")
         Eb = torch.zeros((T, R), dtype=torch.int64, device="cuda")
         bc = torch.zeros((T, R), dtype=torch.int32, device="cuda")
-        r = S.Result(sig.data_ptr(), hist.data_ptr(), Is.data_ptr(), E.data_ptr(), Eb.data_ptr(), bc.data_ptr())
+        tr = torch.zeros((kw["cycles"], T, R), dtype=torch.int64, device="cuda")
+        r = S.Result(sig.data_ptr(), hist.data_ptr(), Is.data_ptr(), E.data_ptr(), Eb.data_ptr(), bc.data_ptr(),
+                     tr.data_ptr())
         rc = L.ssqa_anneal_noalloc(N, Jd.data_ptr(), hd.data_ptr(), ctypes.byref(p), ctypes.byref(r),
                                    ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, S.last_error()
@@ -68,11 +70,12 @@ def test_noalloc_matches_anneal_twice():
         np.testing.assert_array_equal(E.cpu().numpy(), ref["E_final"])
         np.testing.assert_array_equal(Eb.cpu().numpy(), ref["E_best"])
         np.testing.assert_array_equal(bc.cpu().numpy(), ref["best_cycle"])
+        np.testing.assert_array_equal(tr.cpu().numpy(), ref["E_trace"])
     # a problem beyond the fixed scratch is rejected with a clear error
     I, kw = cases[0]
     Jd, hd, N = _device_inputs(I, torch)
     p = S.make_params(R=128, cycles=1, trials=20000, seed=1)
     p.flags = S.FLAG_DEVICE_PTRS
-    r = S.Result(Jd.data_ptr(), None, hd.data_ptr(), None, None, None)
+    r = S.Result(Jd.data_ptr(), None, hd.data_ptr(), None, None, None, None)
     assert L.ssqa_anneal_noalloc(N, Jd.data_ptr(), hd.data_ptr(), ctypes.byref(p), ctypes.byref(r), None) == S.ERR_INVALID_ARG
     assert "scratch" in S.last_error()
