@@ -184,25 +184,36 @@ def make_params(*, R: int, cycles: int, trials: int, seed: int, **kw) -> Params:
 
 
 def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_best: bool = False,
-           state=None, want_hist: bool = False, want_trace: bool = False, stream=None, **kw):
+           state=None, want_hist: bool = False, want_trace: bool = False, stream=None, out=None, **kw):
     """Anneal with host buffers; returns numpy arrays (sigma, Is, E_final, ...).
     want_trace (implies track_best): E_trace [cycles, trials, R], the energy of
-    every replica after every cycle."""
+    every replica after every cycle.  out: optional dict of caller-owned result
+    arrays to fill instead of fresh ones (sigma int8 [T,R,N], Is int32 [T,R,N],
+    E_final int64 [T,R]), e.g. pinned buffers reused across calls."""
     track_best = track_best or want_trace
     N = ising.N
     p = make_params(R=R, cycles=cycles, trials=trials, seed=seed, **kw)
     if track_best:
         p.flags |= FLAG_TRACK_BEST
     d = p.delay
-    sigma = np.zeros((trials, R, N), np.int8)
-    Is = np.zeros((trials, R, N), np.int32)
+
+    def _buf(key, shape, dtype):
+        if out is not None and key in out:
+            a = out[key]
+            if a.shape != shape or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"out[{key!r}] must be a C-contiguous {np.dtype(dtype)} array of shape {shape}")
+            return a
+        return np.zeros(shape, dtype)
+
+    sigma = _buf("sigma", (trials, R, N), np.int8)
+    Is = _buf("Is", (trials, R, N), np.int32)
     hist = np.zeros((trials, d, R, N), np.int8) if (d and (want_hist or state is not None)) else None
     if state is not None:
         sigma[...] = state["sigma"]
         Is[...] = state["Is"]
         if hist is not None:
             hist[...] = state["hist"]
-    E = np.zeros((trials, R), np.int64)
+    E = _buf("E_final", (trials, R), np.int64)
     Eb = np.zeros((trials, R), np.int64) if track_best else None
     bc = np.zeros((trials, R), np.int32) if track_best else None
     tr = np.zeros((cycles, trials, R), np.int64) if want_trace else None

@@ -125,3 +125,15 @@ def test_compute_calls_fail_loudly_without_gpu():
 def test_params_default_is_table2():
     p = S.make_params(R=25, cycles=1600, trials=100, seed=0)
     assert (p.I0, p.alpha, p.n_rnd, p.jperp_min, p.jperp_max, p.beta, p.tau, p.delay) == (24, 1, 12, 0, 6, 3, 100, 1)
+
+
+def test_anneal_out_buffers_are_checked():
+    """Caller-owned result arrays (out=) must have the result's shape, dtype
+    and layout; a mismatch is rejected before any device work."""
+    a = S.gen_er_graph(4, W.p_q32(0.5), 1)
+    b, _ = S.permute_graph(a, 2)
+    I = S.Ising.gi(a, b)
+    for bad in ({"sigma": np.zeros((2, 3, 15), np.int8)}, {"Is": np.zeros((2, 3, 16), np.int64)},
+                {"E_final": np.zeros((3, 2), np.int64)}, {"sigma": np.zeros((2, 16, 3), np.int8).transpose(0, 2, 1)}):
+        with pytest.raises(ValueError):
+            S.anneal(I, R=3, cycles=1, trials=2, seed=1, out=bad)
