@@ -159,6 +159,7 @@ void prepare_tc(ssqa_ising *I) {
             t.why = "row sums of |J|/jm + |h|/jm exceed 2^14";
             return;
         }
+        t.max_row_sum = std::max(t.max_row_sum, s);
     }
     for (size_t i = 0; i < size_t(N) * N; ++i)
         if (I->J[i] && e4m3_of_int(I->J[i] / g) < 0) {

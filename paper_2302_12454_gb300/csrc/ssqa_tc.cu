@@ -18,12 +18,12 @@ namespace ssqa {
 namespace {
 using namespace tc;
 
-KernelFn pick(int d, bool both, bool track, bool fast) {
+KernelFn pick(int d, bool both, bool track, bool fast, bool f16) {
     switch (d) {
-        case 0: return pick_d0(both, track, fast);
-        case 1: return pick_d1(both, track, fast);
-        case 2: return pick_d2(both, track, fast);
-        default: return pick_d3(both, track, fast);
+        case 0: return pick_d0(both, track, fast, f16);
+        case 1: return pick_d1(both, track, fast, f16);
+        case 2: return pick_d2(both, track, fast, f16);
+        default: return pick_d3(both, track, fast, f16);
     }
 }
 
@@ -141,10 +141,16 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.G = L.G;
     p.crow[0] = img.chunk_rows[0];
     p.crow[1] = img.chunk_rows[1];
+    // fast variant: R divides 32, counters fit a biased byte, alpha = 1, and
+    // a fresh start (resumed counters may lie outside the byte range)
+    const int32_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
+    const bool fast = (32 % a.R == 0) && i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
+    // FP16 accumulator when every partial sum is an integer of magnitude <= 2048
+    const bool f16 = fast && img.max_row_sum <= 2048;
     for (int ch = 0; ch < 2; ++ch) {
-        // instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B
-        // E4M3 (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-        p.idesc[ch] = (1u << 4) | (uint32_t(img.chunk_rows[ch] >> 3) << 17) | (uint32_t(kCT >> 4) << 24);
+        // instruction descriptor, kind::f8f6f4: D f16 (bits 4-5 = 0) or f32 (1),
+        // A and B E4M3 (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+        p.idesc[ch] = ((f16 ? 0u : 1u) << 4) | (uint32_t(img.chunk_rows[ch] >> 3) << 17) | (uint32_t(kCT >> 4) << 24);
     }
     uint32_t tc = 32;
     while (tc < uint32_t(img.Brows)) tc <<= 1;
@@ -152,10 +158,6 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     for (int m = 0; m < img.nh; ++m) p.a_w[m] = img.a_w[m];
     p.JM2 = half2_bits(float(img.jm));
     p.NR2 = half2_bits(float(a.n_rnd));
-    // fast variant: R divides 32, counters fit a biased byte, alpha = 1, and
-    // a fresh start (resumed counters may lie outside the byte range)
-    const int32_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
-    const bool fast = (32 % a.R == 0) && i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
     p.bias = fast ? 1152.f : 0.f;
     p.i0_levels = 1;
     p.i0_mult = 2;
@@ -178,7 +180,7 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     if (e) return fail(SSQA_ERR_OOM, std::string("tensor path: ") + cudaGetErrorString(e));
     cudaMemsetAsync(err, 0, sizeof(int), st);
     p.err = err;
-    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, fast);
+    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, fast, f16);
     configure_once(fn);
     const int64_t grid = (int64_t(a.trials) + L.Tb - 1) / L.Tb;
     fn<<<unsigned(grid), kThreads, L.total, st>>>(p);

@@ -141,6 +141,18 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[16]) {
                    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
                    "+r"(r[15])::"memory");
 }
+// 32 lanes x 16 consecutive 16-bit TMEM columns (an FP16 accumulator), packed
+// two per register (column 2i in the low half), issued without waiting.
+__device__ __forceinline__ void tmem_ld16h_issue(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.pack::16b.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait8(uint32_t (&r)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])::"memory");
+}
 // Shared-memory matrix descriptor (tcgen05), no swizzle, K-major:
 // core matrices of 8 rows x 16 bytes; LBO = stride between K-adjacent core
 // matrices, SBO = stride between 8-row groups; version field = 1.
@@ -202,7 +214,10 @@ __device__ __forceinline__ uint32_t word_bit(uint32_t w, uint32_t i) { return (w
 // history through a shared-memory slot and applies Eq. 6b with a compare.
 // In both, counters are handled in FP16 with an offset `bias` (1152 in the
 // fast variant, where half(1024 + b) holds the byte b exactly, 0 otherwise).
-template <int D, bool kBoth, bool kTrack, bool kFast>
+// kF16 (fast variant only): the accumulator is FP16 (every partial sum is an
+// integer of magnitude <= 2048, exact in FP16), read from TMEM as packed half2
+// pairs, so the epilogue needs no FP32 -> FP16 conversion.
+template <int D, bool kBoth, bool kTrack, bool kFast, bool kF16>
 __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_constant__ TcParams p) {
     constexpr bool kShfl = kFast;
     extern __shared__ uint8_t smem_raw[];
@@ -449,11 +464,16 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
             for (int g = 0; g < kMaxG; ++g) {
                 const int gg = gran_of(g);
                 if (gg >= p.G) break;
-                uint32_t f[16];
+                uint32_t f[kF16 ? 8 : 16];  // FP32 values, or FP16 pairs (kF16)
                 wait_chunk(gg * 16);
                 if (pmask && waited1) flush_pending();
-                tmem_ld16_issue(taddr_lane + uint32_t(gg * 16), f);
-                tmem_ld_wait(f);
+                if constexpr (kF16) {
+                    tmem_ld16h_issue(taddr_lane + uint32_t(gg * 16), f);
+                    tmem_ld_wait8(f);
+                } else {
+                    tmem_ld16_issue(taddr_lane + uint32_t(gg * 16), f);
+                    tmem_ld_wait(f);
+                }
                 const int i0 = gg * 16;
                 const int half = g & 1;
                 const int lw = g >> 1;
@@ -471,8 +491,17 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                         for (int q = 0; q < 8; ++q) {
                             const int j = half * 8 + q;
                             const int i = i0 + 2 * q;
-                            const float y0 = __uint_as_float(f[2 * q]) + (i < a.N ? sh[i] : 0.f);
-                            const float y1 = __uint_as_float(f[2 * q + 1]) + (i + 1 < a.N ? sh[i + 1] : 0.f);
+                            float d0, d1;
+                            if constexpr (kF16) {
+                                const float2 dd = __half22float2(u2h(f[q]));
+                                d0 = dd.x;
+                                d1 = dd.y;
+                            } else {
+                                d0 = __uint_as_float(f[2 * q]);
+                                d1 = __uint_as_float(f[2 * q + 1]);
+                            }
+                            const float y0 = d0 + (i < a.N ? sh[i] : 0.f);
+                            const float y1 = d1 + (i + 1 < a.N ? sh[i + 1] : 0.f);
                             const uint32_t sl = (sw << (16 + j)) & 0x80000000u;
                             const uint32_t shi = (sw << j) & 0x80000000u;
                             esum += __uint_as_float(__float_as_uint(y0) ^ sl);
@@ -491,7 +520,11 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 for (int q = 0; q < 8; ++q) {
                     const int j = half * 8 + q;
                     // Eq. 6a: jm*D = J sigma + h; +- n_rnd (noise); +- J_perp sigma_{k+1}(t - d)
-                    const uint32_t x2 = pack_h2(f[2 * q], f[2 * q + 1]);
+                    uint32_t x2;
+                    if constexpr (kF16)
+                        x2 = f[q];
+                    else
+                        x2 = pack_h2(f[2 * q], f[2 * q + 1]);
                     const uint32_t n2 = ((nw << j) & kSignPair) ^ p.NR2;
                     const uint32_t c2 = ((up_w << j) & kSignPair) ^ JP2;
                     __half2 y = __hfma2(u2h(x2), u2h(p.JM2), u2h(n2));
@@ -652,20 +685,21 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
 using KernelFn = void (*)(TcParams);
 
 // Kernel variants are split over several translation units (one per delay d)
-// so that they compile in parallel.
-KernelFn pick_d0(bool both, bool track, bool fast);
-KernelFn pick_d1(bool both, bool track, bool fast);
-KernelFn pick_d2(bool both, bool track, bool fast);
-KernelFn pick_d3(bool both, bool track, bool fast);
+// so that they compile in parallel.  f16: FP16 accumulator (fast variant only).
+KernelFn pick_d0(bool both, bool track, bool fast, bool f16);
+KernelFn pick_d1(bool both, bool track, bool fast, bool f16);
+KernelFn pick_d2(bool both, bool track, bool fast, bool f16);
+KernelFn pick_d3(bool both, bool track, bool fast, bool f16);
 
-#define SSQA_TC_DEFINE_PICK(DD)                                                                          \
-    KernelFn pick_d##DD(bool both, bool track, bool fast) {                                               \
-        if (fast) {                                                                                       \
-            if (both) return track ? ssqa_tc_kernel<DD, true, true, true> : ssqa_tc_kernel<DD, true, false, true>; \
-            return track ? ssqa_tc_kernel<DD, false, true, true> : ssqa_tc_kernel<DD, false, false, true>;   \
-        }                                                                                                 \
-        if (both) return track ? ssqa_tc_kernel<DD, true, true, false> : ssqa_tc_kernel<DD, true, false, false>; \
-        return track ? ssqa_tc_kernel<DD, false, true, false> : ssqa_tc_kernel<DD, false, false, false>;     \
+#define SSQA_TC_PICK_TRACK(DD, B, F, H) \
+    (track ? ssqa_tc_kernel<DD, B, true, F, H> : ssqa_tc_kernel<DD, B, false, F, H>)
+#define SSQA_TC_DEFINE_PICK(DD)                                                                        \
+    KernelFn pick_d##DD(bool both, bool track, bool fast, bool f16) {                                   \
+        if (fast && f16) return both ? SSQA_TC_PICK_TRACK(DD, true, true, true)                         \
+                                     : SSQA_TC_PICK_TRACK(DD, false, true, true);                       \
+        if (fast) return both ? SSQA_TC_PICK_TRACK(DD, true, true, false)                               \
+                              : SSQA_TC_PICK_TRACK(DD, false, true, false);                             \
+        return both ? SSQA_TC_PICK_TRACK(DD, true, false, false) : SSQA_TC_PICK_TRACK(DD, false, false, false); \
     }
 
 }  // namespace tc
