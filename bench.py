@@ -18,6 +18,7 @@ import multiprocessing as mp
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -197,8 +198,8 @@ def run_ours(args, rank, world):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{rank}.csv")
-                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/ssqa_clocks_{rank}.csv")
+    clk = ClockSampler(args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
+                       else os.path.join(tempfile.gettempdir(), f"ssqa_clocks_r{rank}.csv"))
     wall0 = time.perf_counter()
     with clk:
         for k in range(args.steps):
@@ -367,6 +368,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the two large-instance timings")
+    ap.add_argument("--clocks-csv", default="", help="where to keep the nvidia-smi clock samples ({rank} = rank)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))
