@@ -69,3 +69,28 @@ def test_budget_and_ticket_errors():
     r = srv.poll(t, timeout_ms=-1)
     assert r is not None
     srv.close()
+
+
+def test_mixed_paths_equal_alone():
+    """Resident, streamed and delta requests in flight together (the streamed
+    kernel's clusters share the GPU with resident CTAs and CUDA-core kernels):
+    each served result equals its lone run."""
+    reqs = []
+    for j, (n, R, trials, cycles) in enumerate([(6, 8, 20, 120), (23, 4, 6, 60), (20, 16, 16, 100), (30, 8, 5, 40),
+                                                (45, 4, 3, 30), (12, 16, 9, 80), (50, 2, 4, 25)]):
+        reqs.append((_gi(n, 200 + j), dict(R=R, cycles=cycles, trials=trials, seed=300 + j, tau=10)))
+    # a dense instance whose couplings have no exact FP8 value: delta path
+    rng = np.random.default_rng(5)
+    Jd = np.triu(rng.integers(-1, 2, size=(300, 300)) * 17, 1)
+    Jd = (Jd + Jd.T).astype(np.int8)
+    hd = ((np.arange(300) % 7) * 2 - 5).astype(np.int32)
+    reqs.append((S.Ising.dense(Jd, hd), dict(R=4, cycles=40, trials=3, seed=400, tau=5)))
+    srv = S.Server(hbm_budget=4 << 30, max_slots=8)
+    tickets = [srv.submit(I, track_best=True, **kw) for I, kw in reqs]
+    results = [srv.poll(t, timeout_ms=-1) for t in tickets]
+    for j, (I, kw) in enumerate(reqs):
+        alone = S.anneal(I, track_best=True, want_hist=True, **kw)
+        got, _ = results[j]
+        for k in alone:
+            np.testing.assert_array_equal(got[k], alone[k], err_msg=f"request {j} field {k}")
+    srv.close()
