@@ -18,12 +18,18 @@ namespace ssqa {
 namespace {
 using namespace tc;
 
-KernelFn pick(int d, bool both, bool track, bool fast, bool f16) {
+KernelFn pick(int d, bool both, bool track, bool bytes, bool f16, bool shfl) {
+    if (shfl) switch (d) {
+            case 0: return pick_shfl_d0(both, track, f16);
+            case 1: return pick_shfl_d1(both, track, f16);
+            case 2: return pick_shfl_d2(both, track, f16);
+            default: return pick_shfl_d3(both, track, f16);
+        }
     switch (d) {
-        case 0: return pick_d0(both, track, fast, f16);
-        case 1: return pick_d1(both, track, fast, f16);
-        case 2: return pick_d2(both, track, fast, f16);
-        default: return pick_d3(both, track, fast, f16);
+        case 0: return pick_slot_d0(both, track, bytes, f16);
+        case 1: return pick_slot_d1(both, track, bytes, f16);
+        case 2: return pick_slot_d2(both, track, bytes, f16);
+        default: return pick_slot_d3(both, track, bytes, f16);
     }
 }
 
@@ -141,11 +147,13 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.G = L.G;
     p.crow[0] = img.chunk_rows[0];
     p.crow[1] = img.chunk_rows[1];
-    // fast variant: R divides 32, counters fit a biased byte, alpha = 1, and
-    // a fresh start (resumed counters may lie outside the byte range)
+    // byte counters: counters fit a biased byte, alpha = 1, and a fresh start
+    // (resumed counters may lie outside the byte range); shuffle exchange
+    // when R divides 32; FP16 accumulator when every partial sum is an
+    // integer of magnitude <= 2048
     const int32_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
-    const bool fast = (32 % a.R == 0) && i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
-    // FP16 accumulator when every partial sum is an integer of magnitude <= 2048
+    const bool fast = i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
+    const bool shfl = fast && 32 % a.R == 0;
     const bool f16 = fast && img.max_row_sum <= 2048;
     for (int ch = 0; ch < 2; ++ch) {
         // instruction descriptor, kind::f8f6f4: D f16 (bits 4-5 = 0) or f32 (1),
@@ -180,7 +188,7 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     if (e) return fail(SSQA_ERR_OOM, std::string("tensor path: ") + cudaGetErrorString(e));
     cudaMemsetAsync(err, 0, sizeof(int), st);
     p.err = err;
-    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, fast, f16);
+    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, fast, f16, shfl);
     configure_once(fn);
     const int64_t grid = (int64_t(a.trials) + L.Tb - 1) / L.Tb;
     fn<<<unsigned(grid), kThreads, L.total, st>>>(p);

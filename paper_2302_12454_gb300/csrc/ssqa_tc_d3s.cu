@@ -1,0 +1,9 @@
+// Shared-memory-slot exchange variants of the persistent tensor-core kernel with replica delay d = 3
+// (Eq. 6a, sigma_{i,k+1}(t - d)).
+#include "ssqa_tc_kernel.cuh"
+
+namespace ssqa {
+namespace tc {
+SSQA_TC_DEFINE_PICK_SLOT(3)
+}  // namespace tc
+}  // namespace ssqa

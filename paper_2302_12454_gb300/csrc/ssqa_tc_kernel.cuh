@@ -207,19 +207,19 @@ __device__ __forceinline__ uint4 mask_tail(uint4 b, int i0, int N) {
 __device__ __forceinline__ uint32_t word_bit(uint32_t w, uint32_t i) { return (w >> spin_bit_pos(i)) & 1u; }
 
 // ------------------------------------------------------------------- kernel
-// kFast: R divides 32 (ring neighbours are lanes of the same warp, spin
-// history exchanged by shuffles), I0 <= 127 (each counter Is kept as the
-// byte Is + 128, four per register) and alpha = 1 (the counter update is a
-// clamp).  The general variant keeps the counters as half2, exchanges the
-// history through a shared-memory slot and applies Eq. 6b with a compare.
-// In both, counters are handled in FP16 with an offset `bias` (1152 in the
-// fast variant, where half(1024 + b) holds the byte b exactly, 0 otherwise).
-// kF16 (fast variant only): the accumulator is FP16 (every partial sum is an
+// kFast (byte counters): I0 <= 127 (each counter Is kept as the byte Is + 128,
+// four per register) and alpha = 1 (the counter update is a clamp).  Otherwise
+// the counters are half2 and Eq. 6b is applied with a compare.  In both,
+// counters are handled in FP16 with an offset `bias` (1152 for byte counters,
+// where half(1024 + b) holds the byte b exactly, 0 otherwise).
+// kShfl (byte counters and R dividing 32): ring neighbours are lanes of the
+// same warp and the spin history is exchanged by shuffles; otherwise through a
+// shared-memory slot, with a barrier before it is rewritten.
+// kF16 (byte counters only): the accumulator is FP16 (every partial sum is an
 // integer of magnitude <= 2048, exact in FP16), read from TMEM as packed half2
 // pairs, so the epilogue needs no FP32 -> FP16 conversion.
-template <int D, bool kBoth, bool kTrack, bool kFast, bool kF16>
+template <int D, bool kBoth, bool kTrack, bool kFast, bool kF16, bool kShfl>
 __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_constant__ TcParams p) {
-    constexpr bool kShfl = kFast;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = sm + p.smem_A;
@@ -684,22 +684,34 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
 
 using KernelFn = void (*)(TcParams);
 
-// Kernel variants are split over several translation units (one per delay d)
-// so that they compile in parallel.  f16: FP16 accumulator (fast variant only).
-KernelFn pick_d0(bool both, bool track, bool fast, bool f16);
-KernelFn pick_d1(bool both, bool track, bool fast, bool f16);
-KernelFn pick_d2(bool both, bool track, bool fast, bool f16);
-KernelFn pick_d3(bool both, bool track, bool fast, bool f16);
+// Kernel variants are split over several translation units (per delay d, and
+// shuffle vs shared-memory-slot exchange) so that they compile in parallel.
+// f16: FP16 accumulator (byte counters only).
+KernelFn pick_shfl_d0(bool both, bool track, bool f16);
+KernelFn pick_shfl_d1(bool both, bool track, bool f16);
+KernelFn pick_shfl_d2(bool both, bool track, bool f16);
+KernelFn pick_shfl_d3(bool both, bool track, bool f16);
+KernelFn pick_slot_d0(bool both, bool track, bool bytes, bool f16);
+KernelFn pick_slot_d1(bool both, bool track, bool bytes, bool f16);
+KernelFn pick_slot_d2(bool both, bool track, bool bytes, bool f16);
+KernelFn pick_slot_d3(bool both, bool track, bool bytes, bool f16);
 
-#define SSQA_TC_PICK_TRACK(DD, B, F, H) \
-    (track ? ssqa_tc_kernel<DD, B, true, F, H> : ssqa_tc_kernel<DD, B, false, F, H>)
-#define SSQA_TC_DEFINE_PICK(DD)                                                                        \
-    KernelFn pick_d##DD(bool both, bool track, bool fast, bool f16) {                                   \
-        if (fast && f16) return both ? SSQA_TC_PICK_TRACK(DD, true, true, true)                         \
-                                     : SSQA_TC_PICK_TRACK(DD, false, true, true);                       \
-        if (fast) return both ? SSQA_TC_PICK_TRACK(DD, true, true, false)                               \
-                              : SSQA_TC_PICK_TRACK(DD, false, true, false);                             \
-        return both ? SSQA_TC_PICK_TRACK(DD, true, false, false) : SSQA_TC_PICK_TRACK(DD, false, false, false); \
+#define SSQA_TC_PICK_TRACK(DD, B, F, H, S) \
+    (track ? ssqa_tc_kernel<DD, B, true, F, H, S> : ssqa_tc_kernel<DD, B, false, F, H, S>)
+#define SSQA_TC_DEFINE_PICK_SHFL(DD)                                                                   \
+    KernelFn pick_shfl_d##DD(bool both, bool track, bool f16) {                                         \
+        if (f16) return both ? SSQA_TC_PICK_TRACK(DD, true, true, true, true)                          \
+                             : SSQA_TC_PICK_TRACK(DD, false, true, true, true);                        \
+        return both ? SSQA_TC_PICK_TRACK(DD, true, true, false, true) : SSQA_TC_PICK_TRACK(DD, false, true, false, true); \
+    }
+#define SSQA_TC_DEFINE_PICK_SLOT(DD)                                                                   \
+    KernelFn pick_slot_d##DD(bool both, bool track, bool bytes, bool f16) {                             \
+        if (bytes && f16) return both ? SSQA_TC_PICK_TRACK(DD, true, true, true, false)                \
+                                      : SSQA_TC_PICK_TRACK(DD, false, true, true, false);              \
+        if (bytes) return both ? SSQA_TC_PICK_TRACK(DD, true, true, false, false)                      \
+                               : SSQA_TC_PICK_TRACK(DD, false, true, false, false);                    \
+        return both ? SSQA_TC_PICK_TRACK(DD, true, false, false, false)                                \
+                    : SSQA_TC_PICK_TRACK(DD, false, false, false, false);                              \
     }
 
 }  // namespace tc
