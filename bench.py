@@ -116,11 +116,12 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- our arm
-def large_workloads(S, W, torch, stream):
+def large_workloads(S, W, torch, stream, cores=0):
     """The two large configurations (one anneal each, default path = the
     streamed tensor kernel), timed with CUDA events after a warm-up call that
     uploads the instance.  Informational: the headline is the batched N = 400
-    workload."""
+    workload.  With `cores`, also the oracle's rate on a bounded sample of the
+    same instance (one trial per core, a few cycles), per spin update."""
     res = {}
     for name in ("large_gi_n50", "sk_n8192"):
         cfg = dict(W.CONFIGS[name])
@@ -151,6 +152,11 @@ def large_workloads(S, W, torch, stream):
              "tflops": 2.0 * N * N * R * T * C / t / 1e12}
         if cfg["kind"] == "gi":
             r["p_s"] = float((E.min(dim=1).values.cpu().numpy() == -off).mean())
+        if cores:
+            oc = 2 if cfg["kind"] == "gi" else 1
+            rate, wall = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, oc, cores, cores)
+            r["oracle"] = {"value": rate, "unit": "spin-updates/s", "cores": cores,
+                           "sample": f"{cores} trials x {oc} cycles ({wall:.1f} s)", "ratio": r["value"] / rate}
         res[name] = r
         del I
     return res
@@ -315,13 +321,16 @@ def run_ours(args, rank, world):
         out["served"] = SB.run(S, W, count=64, n_min=8, n_max=20, cycles_set=(500, 1000, 2000), slots=32,
                                plain_sample=8)
         if not args.no_large:
-            out["large_workloads"] = large_workloads(S, W, torch, stream)
+            out["large_workloads"] = large_workloads(S, W, torch, stream,
+                                                     0 if args.no_cpu_baseline else min(16, os.cpu_count() or 1))
         if not args.no_cpu_baseline:
             cores = min(16, os.cpu_count() or 1)
             rate, cwall = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, cycles, 2 * cores, cores)
+            rate1, wall1 = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, 500, 1, 1)
             out["cpu_baseline"] = {"value": rate, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
                                    "sample": f"{2 * cores} trials x {cycles} cycles of the same workload, one "
-                                             f"single-threaded oracle process per core ({cwall:.1f} s)"}
+                                             f"single-threaded oracle process per core ({cwall:.1f} s)",
+                                   "single_core": {"value": rate1, "sample": f"1 trial x 500 cycles ({wall1:.1f} s)"}}
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

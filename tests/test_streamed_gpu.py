@@ -144,7 +144,7 @@ def test_large_gi_n50_full_trials():
     for k in ("sigma", "Is", "E_final", "E_best", "best_cycle"):
         np.testing.assert_array_equal(g[k], de[k], err_msg=k)
     h, J, _ = I.export()
-    for tr in (0, c["trials"] - 1):
+    for tr in (0, 85, 170, c["trials"] - 1):
         o = O.anneal(h, J, R=c["R"], cycles=30, trials=1, seed=c["seed"], tau=c["tau"], trial_offset=tr,
                      track_best=True)
         for k in ("sigma", "Is", "E_final", "E_best", "best_cycle"):
@@ -160,9 +160,10 @@ def test_sk_n8192_full_trials():
     for k in ("sigma", "Is", "E_final"):
         np.testing.assert_array_equal(g[k], de[k], err_msg=k)
     h, J, _ = I.export()
-    o = O.anneal(h, J, R=c["R"], cycles=3, trials=1, seed=c["seed"], tau=c["tau"], trial_offset=c["trials"] - 1)
-    for k in ("sigma", "Is", "E_final"):
-        np.testing.assert_array_equal(g[k][-1:], o[k], err_msg=k)
+    for tr in (0, 21, 42, c["trials"] - 1):
+        o = O.anneal(h, J, R=c["R"], cycles=3, trials=1, seed=c["seed"], tau=c["tau"], trial_offset=tr)
+        for k in ("sigma", "Is", "E_final"):
+            np.testing.assert_array_equal(g[k][tr:tr + 1], o[k], err_msg=k)
 
 
 @pytest.mark.parametrize("case", ["dummy_steps", "padded_groups"])
