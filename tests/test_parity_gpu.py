@@ -242,3 +242,17 @@ def test_ssqa_with_i0_schedule_bit_exact(algo):
     g, o = both_runs(I, algo, R=8, cycles=120, trials=5, seed=63, tau=7, I0=12, i0_max=96, i0_mult=2, i0_tau=9,
                      track=True)
     assert_same(g, o, track=True)
+
+
+def test_resume_with_counters_beyond_a_byte():
+    # a state from a run with I0' = 400 holds counters outside -128..127: the
+    # resident kernel then keeps them as half2 (byte counters otherwise)
+    I = gi(9, 0.5, 71, 72)
+    h, J, off = I.export()
+    big = S.anneal(I, R=4, cycles=40, trials=3, seed=2, algo=S.ALGO_DELTA, I0=400, n_rnd=300, want_hist=True)
+    assert np.abs(big["Is"]).max() > 127
+    kw = dict(R=4, cycles=20, trials=3, seed=2, tau=5, start_cycle=40)
+    g = S.anneal(I, algo=S.ALGO_TENSOR, init_mode=S.INIT_FROM_STATE, state=big, want_hist=True, **kw)
+    o = O.anneal(h, J, init_mode=2, state=dict(sigma=big["sigma"], Is=big["Is"], hist=big["hist"]), **kw)
+    for k in ("sigma", "Is", "E_final", "hist"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
