@@ -162,6 +162,72 @@ def large_workloads(S, W, torch, stream, cores=0):
     return res
 
 
+def row_timings(S, torch, stream, I, cfg, sigma, Is, E, base_ms):
+    """The rows the headline step leaves out, timed on the same instance and
+    batch (CUDA events, best of three after a warm-up call):
+    - energy tracking: lowest energy and its cycle per replica, from the
+      energy fused into every cycle's epilogue;
+    - energy trace: the same plus every replica's energy after every cycle
+      ([cycles][trials * R] int64 written to device memory);
+    - SSA mode: R = 1 with the I0 schedule (I0' = 12 .. 192 doubling every 10
+      cycles, n_rnd' = 12, no J_perp), one column per trial, same column count;
+    - ssqa_energy on the final spins of the headline step (every column),
+      checked against the anneal's own final energies."""
+    import ctypes
+
+    N, R, T, C = I.N, cfg["R"], cfg["trials"], cfg["cycles"]
+    cols = T * R
+    dev = sigma.device
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    def row(ms, updates, what):
+        return {"ms": ms, "value": updates / (ms / 1e3), "unit": "spin-updates/s", "vs_headline_step": ms / base_ms,
+                "what": what}
+
+    out = {}
+    Eb = torch.empty((T, R), dtype=torch.int64, device=dev)
+    bc = torch.empty((T, R), dtype=torch.int32, device=dev)
+    pt = S.make_params(R=R, cycles=C, trials=T, seed=cfg["seed"], tau=cfg["tau"], algo=S.ALGO_TENSOR)
+    ms = timed(lambda: S.anneal_device(I, pt, sigma, Is, e_final=E, e_best=Eb, best_cycle=bc, stream=stream))
+    out["energy_tracking"] = row(ms, N * cols * C, "headline anneal + per-cycle energy, best energy and cycle")
+    tr = torch.empty((C, cols), dtype=torch.int64, device=dev)
+    ms = timed(lambda: S.anneal_device(I, pt, sigma, Is, e_final=E, e_best=Eb, best_cycle=bc, stream=stream,
+                                       e_trace=tr))
+    out["energy_trace"] = row(ms, N * cols * C, f"as energy_tracking + trace of {C} x {cols} energies "
+                                                f"({tr.numel() * 8 / 1e6:.0f} MB)")
+    assert torch.equal(tr.min(dim=0).values.view(T, R), Eb)
+    del tr
+    ps = S.make_params(R=1, cycles=C, trials=cols, seed=cfg["seed"], tau=10, beta=3, jperp_min=0, jperp_max=0,
+                       I0=12, i0_max=192, i0_mult=2, i0_tau=10, n_rnd=12, algo=S.ALGO_TENSOR)
+    s1, i1, e1 = sigma.view(cols, 1, N), Is.view(cols, 1, N), E.view(cols, 1)
+    ms = timed(lambda: S.anneal_device(I, ps, s1, i1, e_final=e1, stream=stream))
+    out["ssa"] = row(ms, N * cols * C, f"SSA (R = 1, I0 schedule), {cols} trials x {C} cycles")
+    # final spins and energies of one headline step, then ssqa_energy on them
+    S.anneal_device(I, pt, sigma, Is, e_final=E, e_best=Eb, best_cycle=bc, stream=stream)
+    E2 = torch.empty(cols, dtype=torch.int64, device=dev)
+    h = ctypes.c_void_p(stream.cuda_stream)
+    call = lambda: S._check(S.lib().ssqa_energy(I.handle, ctypes.c_void_p(sigma.data_ptr()), cols,  # noqa: E731
+                                                 ctypes.c_void_p(E2.data_ptr()), S.FLAG_DEVICE_PTRS, h), "energy")
+    ms = timed(call)
+    assert torch.equal(E2.view(T, R), E)
+    out["energy_call"] = {"ms": ms, "value": cols / (ms / 1e3), "unit": "configurations/s",
+                          "what": f"ssqa_energy of {cols} spin vectors of N = {N} (device pointers)"}
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -237,9 +303,10 @@ def run_ours(args, rank, world):
     # anneal, result download inside the timed region (pinned host memory)
     hJ = torch.from_numpy(J).pin_memory().numpy()
     hh = torch.from_numpy(h).pin_memory().numpy()
-    # result buffers: pinned host memory, allocated once and reused by every call
+    # result buffers: pinned host memory, allocated once and reused by every
+    # call; the step's result is the final spins and energies (the counters
+    # Is are only needed to resume and are not read back)
     hout = {"sigma": torch.empty((trials, R, N), dtype=torch.int8, pin_memory=True).numpy(),
-            "Is": torch.empty((trials, R, N), dtype=torch.int32, pin_memory=True).numpy(),
             "E_final": torch.empty((trials, R), dtype=torch.int64, pin_memory=True).numpy()}
     e2e_t = []
     for k in range(max(1, min(args.steps, 3)) + 1):
@@ -247,13 +314,13 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         Ik = S.Ising.dense(hJ, hh, off)
         outk = S.anneal(Ik, R=R, cycles=cycles, trials=trials, seed=cfg["seed"], tau=cfg["tau"],
-                        trial_offset=offset, algo=S.ALGO_TENSOR, out=hout)
+                        trial_offset=offset, algo=S.ALGO_TENSOR, want_state=False, out=hout)
         e2e_t.append(time.perf_counter() - t0)
         del Ik
     e2e_t = e2e_t[1:]  # first call includes one-time context and allocator set-up
     e2e_val = updates_per_step * world / float(np.mean(e2e_t))
     h2d = J.nbytes + h.nbytes  # the step's inputs: couplings and biases (device images derive from them)
-    d2h = outk["sigma"].nbytes + outk["Is"].nbytes + outk["E_final"].nbytes
+    d2h = outk["sigma"].nbytes + outk["E_final"].nbytes
     assert np.array_equal(outk["E_final"].min(axis=1) == -off, e_min == -off)
 
     # plain GPU path (one kernel launch per cycle, CUDA-core dot products) on
@@ -320,6 +387,7 @@ def run_ours(args, rank, world):
 
         out["served"] = SB.run(S, W, count=64, n_min=8, n_max=20, cycles_set=(500, 1000, 2000), slots=32,
                                plain_sample=8)
+        out["rows"] = row_timings(S, torch, stream, I, cfg, sigma, Is, E, ms_per_step)
         if not args.no_large:
             out["large_workloads"] = large_workloads(S, W, torch, stream,
                                                      0 if args.no_cpu_baseline else min(16, os.cpu_count() or 1))

@@ -182,7 +182,9 @@ void ssqa_params_default(ssqa_params *p);
  *              out always, in when resuming; may be NULL if delay == 0 or if
  *              neither resuming nor checkpointing.
  *   is_state   [trials][R][N] int32: counter Is (Eq. 6b), out; in when
- *              resuming.                                         (required)
+ *              resuming.  Required with SSQA_FLAG_DEVICE_PTRS and when
+ *              resuming; otherwise may be NULL, and the counters are then
+ *              not returned (the anneal itself is unchanged).
  *   e_final    [trials][R] int64: E'(sigma(t0+cycles)) of Eq. 5 per
  *              replica; may be NULL.
  *   e_best     [trials][R] int64 and best_cycle [trials][R] int32: lowest

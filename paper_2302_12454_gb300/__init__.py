@@ -184,12 +184,15 @@ def make_params(*, R: int, cycles: int, trials: int, seed: int, **kw) -> Params:
 
 
 def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_best: bool = False,
-           state=None, want_hist: bool = False, want_trace: bool = False, stream=None, out=None, **kw):
+           state=None, want_hist: bool = False, want_trace: bool = False, want_state: bool = True, stream=None,
+           out=None, **kw):
     """Anneal with host buffers; returns numpy arrays (sigma, Is, E_final, ...).
     want_trace (implies track_best): E_trace [cycles, trials, R], the energy of
-    every replica after every cycle.  out: optional dict of caller-owned result
-    arrays to fill instead of fresh ones (sigma int8 [T,R,N], Is int32 [T,R,N],
-    E_final int64 [T,R]), e.g. pinned buffers reused across calls."""
+    every replica after every cycle.  want_state=False: the counters Is are not
+    returned (nor copied back); needed only to resume.  out: optional dict of
+    caller-owned result arrays to fill instead of fresh ones (sigma int8
+    [T,R,N], Is int32 [T,R,N], E_final int64 [T,R]), e.g. pinned buffers
+    reused across calls."""
     track_best = track_best or want_trace
     N = ising.N
     p = make_params(R=R, cycles=cycles, trials=trials, seed=seed, **kw)
@@ -206,7 +209,9 @@ def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_b
         return np.zeros(shape, dtype)
 
     sigma = _buf("sigma", (trials, R, N), np.int8)
-    Is = _buf("Is", (trials, R, N), np.int32)
+    if state is not None and not want_state:
+        raise ValueError("resuming (state=...) needs want_state=True")
+    Is = _buf("Is", (trials, R, N), np.int32) if want_state else None
     hist = np.zeros((trials, d, R, N), np.int8) if (d and (want_hist or state is not None)) else None
     if state is not None:
         sigma[...] = state["sigma"]
@@ -220,7 +225,9 @@ def anneal(ising: Ising, *, R: int, cycles: int, trials: int, seed: int, track_b
     r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(E), _ptr(Eb), _ptr(bc), _ptr(tr))
     st = None if stream is None else ctypes.c_void_p(int(stream))
     _check(lib().ssqa_anneal(ising.handle, ctypes.byref(p), ctypes.byref(r), st), "anneal")
-    out = dict(sigma=sigma, Is=Is, E_final=E)
+    out = dict(sigma=sigma, E_final=E)
+    if want_state:
+        out["Is"] = Is
     if hist is not None:
         out["hist"] = hist
     if track_best:

@@ -127,8 +127,14 @@ int64_t gcd64(int64_t a, int64_t b) {
 void prepare_tc(ssqa_ising *I) {
     TcImage &t = I->tc;
     const int N = I->N;
+    const size_t NN = size_t(N) * N;
+    // J is int8: the common factor, |J| / jm and the FP8 codes are taken once
+    // per distinct value (at most 256), then looked up per coupling
+    bool present[256] = {};
+    for (size_t x = 0; x < NN; ++x) present[uint8_t(I->J[x])] = true;
     int64_t g = 0;
-    for (int8_t v : I->J) g = gcd64(g, v);
+    for (int v = -128; v < 128; ++v)
+        if (present[uint8_t(v)]) g = gcd64(g, v);
     for (int32_t v : I->h) g = gcd64(g, v);
     if (g == 0) g = 1;
     if (g > 2048) {
@@ -136,6 +142,12 @@ void prepare_tc(ssqa_ising *I) {
         return;
     }
     t.jm = int32_t(g);
+    int64_t mag[256];  // |v / jm| of every int8 value v
+    int code[256];     // E4M3 code of v / jm, -1 if none (v = 0 -> 0)
+    for (int v = -128; v < 128; ++v) {
+        mag[uint8_t(v)] = std::llabs(v / g);
+        code[uint8_t(v)] = v % g ? -1 : e4m3_of_int(v / g);
+    }
     t.h_unit.resize(N);
     int64_t hmax = 0;
     for (int i = 0; i < N; ++i) {
@@ -154,15 +166,16 @@ void prepare_tc(ssqa_ising *I) {
     // accumulator bound: every partial sum of D stays an exact small integer
     for (int i = 0; i < N; ++i) {
         int64_t s = std::llabs(t.h_unit[i]);
-        for (int j = 0; j < N; ++j) s += std::llabs(I->J[size_t(i) * N + j] / g);
+        const int8_t *row = I->J.data() + size_t(i) * N;
+        for (int j = 0; j < N; ++j) s += mag[uint8_t(row[j])];
         if (s > 16384) {
             t.why = "row sums of |J|/jm + |h|/jm exceed 2^14";
             return;
         }
         t.max_row_sum = std::max(t.max_row_sum, s);
     }
-    for (size_t i = 0; i < size_t(N) * N; ++i)
-        if (I->J[i] && e4m3_of_int(I->J[i] / g) < 0) {
+    for (int v = -128; v < 128; ++v)
+        if (present[uint8_t(v)] && code[uint8_t(v)] < 0) {
             t.why = "a coupling J/jm has no exact FP8 E4M3 value";
             return;
         }
@@ -189,9 +202,11 @@ void prepare_tc(ssqa_ising *I) {
                    size_t(kk % 16);
         };
         for (int i = 0; i < N; ++i) {
-            for (int j = 0; j < N; ++j) {
-                const int8_t v = I->J[size_t(i) * N + j];
-                if (v) t.bs[boff(i, j)] = uint8_t(e4m3_of_int(v / g));
+            const int8_t *row = I->J.data() + size_t(i) * N;
+            for (int j0 = 0; j0 < N; j0 += 16) {  // 16 consecutive K bytes are contiguous
+                uint8_t *dst = t.bs.data() + boff(i, j0);
+                const int n = std::min(16, N - j0);
+                for (int k = 0; k < n; ++k) dst[k] = uint8_t(code[uint8_t(row[j0 + k])]);
             }
             for (int m = 0; m < nh; ++m) t.bs[boff(i, t.N16 + m)] = hdigit(i, m);
         }
@@ -215,18 +230,14 @@ void prepare_tc(ssqa_ising *I) {
         return size_t(r / 8) * (size_t(Kp) * 8) + size_t(k / 16) * 128 + size_t(r % 8) * 16 + size_t(k % 16);
     };
     t.b.assign(size_t(t.Brows) * Kp, 0);
-    for (int i = 0; i < N; ++i)
-        for (int j = 0; j < N; ++j) {
-            int8_t v = I->J[size_t(i) * N + j];
-            if (!v) continue;
-            int code = e4m3_of_int(v / g);
-            if (code < 0) {
-                t.why = "a coupling J/jm has no exact FP8 E4M3 value";
-                t.b.clear();
-                return;
-            }
-            t.b[off(i, j)] = uint8_t(code);
+    for (int i = 0; i < N; ++i) {
+        const int8_t *row = I->J.data() + size_t(i) * N;
+        for (int j0 = 0; j0 < N; j0 += 16) {  // 16 consecutive K bytes are contiguous
+            uint8_t *dst = t.b.data() + off(i, j0);
+            const int n = std::min(16, N - j0);
+            for (int k = 0; k < n; ++k) dst[k] = uint8_t(code[uint8_t(row[j0 + k])]);
         }
+    }
     for (int i = 0; i < N; ++i)
         for (int m = 0; m < nh; ++m) t.b[off(i, t.N16 + m)] = hdigit(i, m);
     t.ok = true;
@@ -399,12 +410,17 @@ int ssqa_ising_from_dense(int32_t N, const int8_t *J, const int32_t *h, int64_t 
     if (!out) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: out is NULL");
     *out = nullptr;
     if (N < 1 || N > 65536 || !J || !h) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: bad N, J or h");
-    for (int32_t i = 0; i < N; ++i) {
+    for (int32_t i = 0; i < N; ++i)
         if (J[size_t(i) * N + i]) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: J diagonal must be 0");
-        for (int32_t j = i + 1; j < N; ++j)
-            if (J[size_t(i) * N + j] != J[size_t(j) * N + i])
-                return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: J must be symmetric");
-    }
+    // symmetry, compared in 32 x 32 tiles (both tiles stay in cache)
+    for (int32_t i0 = 0; i0 < N; i0 += 32)
+        for (int32_t j0 = i0; j0 < N; j0 += 32) {
+            bool sym = true;
+            for (int32_t i = i0; i < std::min(i0 + 32, N); ++i)
+                for (int32_t j = j0; j < std::min(j0 + 32, N); ++j)
+                    sym &= J[size_t(i) * N + j] == J[size_t(j) * N + i];
+            if (!sym) return fail(SSQA_ERR_INVALID_ARG, "ssqa_ising_from_dense: J must be symmetric");
+        }
     std::unique_ptr<ssqa_ising> I(new_ising(N));
     if (!I) return fail(SSQA_ERR_OOM, "ssqa_ising_from_dense: out of host memory");
     std::memcpy(I->J.data(), J, size_t(N) * N);
@@ -503,7 +519,9 @@ int validate(const ssqa_ising *I, const ssqa_params *p, const ssqa_result *r) {
         return fail(SSQA_ERR_INVALID_ARG, "cycle range must stay below 2^32 - 1");
     if (int64_t(p->trial_offset) + p->trials > 0xFFFFFFFFll)
         return fail(SSQA_ERR_INVALID_ARG, "trial_offset + trials must fit 32 bits");
-    if (!r->sigma || !r->is_state) return fail(SSQA_ERR_INVALID_ARG, "sigma and is_state buffers are required");
+    if (!r->sigma) return fail(SSQA_ERR_INVALID_ARG, "the sigma buffer is required");
+    if (!r->is_state && ((p->flags & SSQA_FLAG_DEVICE_PTRS) || p->init_mode == SSQA_INIT_FROM_STATE))
+        return fail(SSQA_ERR_INVALID_ARG, "is_state is required with device pointers and when resuming");
     if (p->init_mode == SSQA_INIT_FROM_STATE && p->delay > 0 && !r->sigma_hist)
         return fail(SSQA_ERR_INVALID_ARG, "resuming with delay > 0 needs sigma_hist");
     if ((p->flags & SSQA_FLAG_TRACK_BEST) && (!r->e_best || !r->best_cycle))
@@ -658,7 +676,7 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     if (rc) return rc;
     if (!devptr) {
         if ((e = cudaMemcpyAsync(r->sigma, a.sigma, nsp, cudaMemcpyDeviceToHost, st)) ||
-            (e = cudaMemcpyAsync(r->is_state, a.Is, nsp * 4, cudaMemcpyDeviceToHost, st)))
+            (r->is_state && (e = cudaMemcpyAsync(r->is_state, a.Is, nsp * 4, cudaMemcpyDeviceToHost, st))))
             return cuda_fail(e, "ssqa_anneal: result download");
         if (r->sigma_hist && a.hist &&
             (e = cudaMemcpyAsync(r->sigma_hist, a.hist, nsp * d, cudaMemcpyDeviceToHost, st)))

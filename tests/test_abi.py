@@ -106,6 +106,28 @@ def test_anneal_argument_checks(bad):
     assert e.value.code == S.ERR_INVALID_ARG
 
 
+def test_counters_are_required_only_to_resume_or_on_device():
+    """is_state may be NULL for a fresh anneal into host buffers; with device
+    pointers or when resuming it is required, which is checked before any
+    device work."""
+    import torch
+    a = O.gen_er_graph(4, W.p_q32(0.5), 1)
+    I = S.Ising.gi(a, a)
+    sig = np.zeros((2, 3, 16), np.int8)
+    for flags, init in ((S.FLAG_DEVICE_PTRS, S.INIT_RANDOM), (0, S.INIT_FROM_STATE)):
+        p = S.make_params(R=3, cycles=1, trials=2, seed=1, init_mode=init, delay=0)
+        p.flags |= flags
+        r = S.Result(S._ptr(sig), None, None, None, None, None, None)
+        assert S.lib().ssqa_anneal(I.handle, ctypes.byref(p), ctypes.byref(r), None) == S.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        S.anneal(I, R=3, cycles=1, trials=2, seed=1, delay=0, want_state=False,
+                 init_mode=S.INIT_FROM_STATE, state={"sigma": sig, "Is": np.zeros((2, 3, 16), np.int32)})
+    if not torch.cuda.is_available():
+        with pytest.raises(S.SSQAError) as e:  # accepted by validation, then no device
+            S.anneal(I, R=3, cycles=1, trials=2, seed=1, want_state=False)
+        assert e.value.code == S.ERR_DEVICE
+
+
 def test_compute_calls_fail_loudly_without_gpu():
     import torch
     if torch.cuda.is_available():

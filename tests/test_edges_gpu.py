@@ -111,3 +111,16 @@ def test_invalid_sizes_are_rejected():
         kw.update(bad)
         with pytest.raises(S.SSQAError):
             S.anneal(I, **kw)
+
+
+@pytest.mark.parametrize("algo", ALL)
+def test_counters_not_returned(algo):
+    """A host anneal without the counter buffer (want_state=False) returns the
+    same spins and energies as one with it, and the oracle's."""
+    I, h, J = dense(40, 7)
+    kw = dict(R=4, cycles=30, trials=3, seed=5, tau=4)
+    g = S.anneal(I, algo=algo, want_state=False, **kw)
+    assert "Is" not in g
+    o = O.anneal(h.astype(np.int64), J.astype(np.int64), **kw)
+    np.testing.assert_array_equal(g["sigma"], o["sigma"])
+    np.testing.assert_array_equal(g["E_final"], o["E_final"])
