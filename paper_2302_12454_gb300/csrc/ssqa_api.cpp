@@ -161,6 +161,7 @@ void prepare_tc(ssqa_ising *I) {
     else if (hmax < 256) nh = 2;
     else nh = 2 + int((hmax / 256 + 14) / 15);
     t.nh = nh;
+    t.max_h_unit = hmax;
     t.N16 = (N + 15) / 16 * 16;
     t.Kp = (t.N16 + nh + 31) / 32 * 32;
     // accumulator bound: every partial sum of D stays an exact small integer

@@ -43,6 +43,7 @@ struct TcImage {
     std::vector<uint8_t> a_w; // e4m3 weights of the h columns (nh bytes)
     std::vector<int32_t> h_unit; // h_i / jm (N)
     int64_t max_row_sum = 0;     // max_i (|h_i| + sum_j |J_ij|) / jm: bound of every partial sum of D
+    int64_t max_h_unit = 0;      // max_i |h_i| / jm
     // Streamed image (instances too large for one SM): B in 256-spin chunks
     // and 32-wide K-blocks, block (ch, kb) of 256 x 32 bytes at
     // (ch * KB + kb) * 8192, element (r, k) at (r/8)*256 + (k/16)*128 + (r%8)*16 + k%16.

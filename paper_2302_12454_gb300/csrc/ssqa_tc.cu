@@ -101,8 +101,8 @@ bool plan(const TcImage &img, const AnnealArgs &a, Layout *L, std::string *why) 
     off += img.Brows * img.Kp;
     L->smem_slot = off;
     off += (kCT * L->WP * 4 + 15) / 16 * 16;
-    L->smem_h = off;
-    off += (a.N * 4 + 15) / 16 * 16;
+    L->smem_h = off;  // h / jm: N floats, or N16 halves (zero beyond N)
+    off += (std::max(a.N * 4, img.N16 * 2) + 15) / 16 * 16;
     L->smem_e = off;
     off += kCT * 8;
     L->smem_bar = off;
@@ -150,11 +150,11 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     // byte counters: counters fit a biased byte, alpha = 1, and a fresh start
     // (resumed counters may lie outside the byte range); shuffle exchange
     // when R divides 32; FP16 accumulator when every partial sum is an
-    // integer of magnitude <= 2048
+    // integer of magnitude <= 2048, and so is D + h / jm (the energy's term)
     const int32_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
     const bool fast = i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
     const bool shfl = fast && 32 % a.R == 0;
-    const bool f16 = fast && img.max_row_sum <= 2048;
+    const bool f16 = fast && img.max_row_sum + img.max_h_unit <= 2048;
     for (int ch = 0; ch < 2; ++ch) {
         // instruction descriptor, kind::f8f6f4: D f16 (bits 4-5 = 0) or f32 (1),
         // A and B E4M3 (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.

@@ -119,6 +119,14 @@ __device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t adesc, uint
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// acc + lo + hi of an FP16 pair, each half converted exactly to FP32.
+__device__ __forceinline__ float add_h2_to_f32(float acc, uint32_t h2) {
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %1;\n\t"
+        "add.rn.f32.f16 %0, lo, %0;\n\tadd.rn.f32.f16 %0, hi, %0;\n\t}"
+        : "+f"(acc)
+        : "r"(h2));
+    return acc;
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -262,7 +270,13 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         const uint4 *g4 = reinterpret_cast<const uint4 *>(p.b_img);
         uint4 *B4 = reinterpret_cast<uint4 *>(sB);
         for (int x = tid; x < p.Brows * Kp / 16; x += kThreads) B4[x] = __ldg(&g4[x]);
-        for (int x = tid; x < a.N; x += kThreads) sh[x] = float(__ldg(&p.h_unit[x]));
+        if constexpr (kF16) {
+            __half *shh = reinterpret_cast<__half *>(sh);
+            for (int x = tid; x < p.N16; x += kThreads)
+                shh[x] = __float2half_rn(x < a.N ? float(__ldg(&p.h_unit[x])) : 0.f);
+        } else {
+            for (int x = tid; x < a.N; x += kThreads) sh[x] = float(__ldg(&p.h_unit[x]));
+        }
         for (int x = tid; x < kCT; x += kThreads) eacc[x] = 0ull;
     }
     tc_fence_before();
@@ -491,21 +505,20 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                         for (int q = 0; q < 8; ++q) {
                             const int j = half * 8 + q;
                             const int i = i0 + 2 * q;
-                            float d0, d1;
                             if constexpr (kF16) {
-                                const float2 dd = __half22float2(u2h(f[q]));
-                                d0 = dd.x;
-                                d1 = dd.y;
+                                // D + h/jm as an FP16 pair (exact: |D_i| + |h_i/jm| <= 2048 on this
+                                // variant; zero beyond N), sign-flipped by sigma, added into FP32
+                                const uint32_t hp = reinterpret_cast<const uint32_t *>(sh)[i >> 1];
+                                const uint32_t y2 = h2u(__hadd2(u2h(f[q]), u2h(hp))) ^ ((sw << j) & kSignPair);
+                                esum = add_h2_to_f32(esum, y2);
                             } else {
-                                d0 = __uint_as_float(f[2 * q]);
-                                d1 = __uint_as_float(f[2 * q + 1]);
+                                const float y0 = __uint_as_float(f[2 * q]) + (i < a.N ? sh[i] : 0.f);
+                                const float y1 = __uint_as_float(f[2 * q + 1]) + (i + 1 < a.N ? sh[i + 1] : 0.f);
+                                const uint32_t sl = (sw << (16 + j)) & 0x80000000u;
+                                const uint32_t shi = (sw << j) & 0x80000000u;
+                                esum += __uint_as_float(__float_as_uint(y0) ^ sl);
+                                esum += __uint_as_float(__float_as_uint(y1) ^ shi);
                             }
-                            const float y0 = d0 + (i < a.N ? sh[i] : 0.f);
-                            const float y1 = d1 + (i + 1 < a.N ? sh[i + 1] : 0.f);
-                            const uint32_t sl = (sw << (16 + j)) & 0x80000000u;
-                            const uint32_t shi = (sw << j) & 0x80000000u;
-                            esum += __uint_as_float(__float_as_uint(y0) ^ sl);
-                            esum += __uint_as_float(__float_as_uint(y1) ^ shi);
                         }
                     }
                     if (!update) continue;
