@@ -251,7 +251,10 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     const int vcols = ntr * a.R;
     const int64_t col0 = trial0 * a.R;  // global column of local column 0
     const bool need_final = a.e_final != nullptr || kTrack;
-    const int iters = a.cycles + (need_final ? 1 : 0);
+    // Tracking variants compute E every cycle, the final one in one more loop
+    // iteration; the others take E(sigma(t0 + cycles)) in a separate pass
+    // after the loop, which keeps the energy code out of the cycle loop.
+    const int iters = a.cycles + (kTrack ? 1 : 0);
 
     // ---------------------------------------------------------------- set-up
     if (tid == 0) {
@@ -396,6 +399,44 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
         bdesc0[1] = smem_desc(smem_u32(sB) + uint32_t(p.crow[0] / 8) * uint32_t(Kp) * 8u, 128u, uint32_t(Kp) * 8u);
     }
     const int ksteps = Kp / 32;
+    // E' = -(jm/2) sum_i sigma_i (D_i + h_i/jm) of one granule (spins i0 ..
+    // i0 + 15, half `half` of the bit word sw = sigma), added to es
+    auto energy_add = [&](const uint32_t (&f)[kF16 ? 8 : 16], const uint32_t sw, const int half, const int i0,
+                          float es) -> float {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = half * 8 + q;
+            const int i = i0 + 2 * q;
+            if constexpr (kF16) {
+                // D + h/jm as an FP16 pair (exact: |D_i| + |h_i/jm| <= 2048 on this
+                // variant; zero beyond N), sign-flipped by sigma, added into FP32
+                const uint32_t hp = reinterpret_cast<const uint32_t *>(sh)[i >> 1];
+                const uint32_t y2 = h2u(__hadd2(u2h(f[q]), u2h(hp))) ^ ((sw << j) & kSignPair);
+                es = add_h2_to_f32(es, y2);
+            } else {
+                const float y0 = __uint_as_float(f[2 * q]) + (i < a.N ? sh[i] : 0.f);
+                const float y1 = __uint_as_float(f[2 * q + 1]) + (i + 1 < a.N ? sh[i + 1] : 0.f);
+                const uint32_t sl = (sw << (16 + j)) & 0x80000000u;
+                const uint32_t shi = (sw << j) & 0x80000000u;
+                es += __uint_as_float(__float_as_uint(y0) ^ sl);
+                es += __uint_as_float(__float_as_uint(y1) ^ shi);
+            }
+        }
+        return es;
+    };
+    // the field product of the current sigma (A), both chunks (issuing lane)
+    auto issue_mmas = [&]() {
+#pragma unroll 1
+        for (int ch = 0; ch < p.nchunk; ++ch) {
+            const uint32_t d_tmem = tmem + uint32_t(ch ? p.crow[0] : 0);
+            const uint32_t idesc = ch ? p.idesc[1] : p.idesc[0];
+            const uint64_t bd0 = ch ? bdesc0[1] : bdesc0[0];
+#pragma unroll 1
+            for (int s = 0; s < ksteps; ++s)
+                mma_f8f6f4(d_tmem, adesc0 + uint64_t(16 * s), bd0 + uint64_t(16 * s), idesc, s > 0 ? 1u : 0u);
+            mma_commit(&bars[ch]);
+        }
+    };
 
     // ------------------------------------------------------------ cycle loop
     // J_perp level of Table 2 tracked incrementally: sub-cycle inside a tau
@@ -412,24 +453,13 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     for (int q = 0; q < ilvl; ++q) i0cur *= p.i0_mult;
     for (int it = 0; it < iters; ++it) {
         const int64_t t = int64_t(a.start_cycle) + it;
-        const bool update = it < a.cycles;
-        const bool energy = (kTrack && it > 0) || !update;
+        const bool update = !kTrack || it < a.cycles;
+        const bool energy = kTrack && (it > 0 || !update);
         const uint32_t parity = uint32_t(it) & 1u;
         if (*abort_flag) break;
         if (mma_warp) {
             tc_fence_after();
-            if (lane == 0) {
-#pragma unroll 1
-                for (int ch = 0; ch < p.nchunk; ++ch) {
-                    const uint32_t d_tmem = tmem + uint32_t(ch ? p.crow[0] : 0);
-                    const uint32_t idesc = ch ? p.idesc[1] : p.idesc[0];
-                    const uint64_t bd0 = ch ? bdesc0[1] : bdesc0[0];
-#pragma unroll 1
-                    for (int s = 0; s < ksteps; ++s)
-                        mma_f8f6f4(d_tmem, adesc0 + uint64_t(16 * s), bd0 + uint64_t(16 * s), idesc, s > 0 ? 1u : 0u);
-                    mma_commit(&bars[ch]);
-                }
-            }
+            if (lane == 0) issue_mmas();
             __syncwarp();
         }
         {
@@ -479,8 +509,12 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 const int gg = gran_of(g);
                 if (gg >= p.G) break;
                 uint32_t f[kF16 ? 8 : 16];  // FP32 values, or FP16 pairs (kF16)
-                wait_chunk(gg * 16);
-                if (pmask && waited1) flush_pending();
+                // Slots >= 4 hold granules >= 16 (spins >= 256 >= the first chunk's end), so
+                // with two chunks the second is awaited by slot 4; with one, by slot 0.
+                if (g <= 4) {
+                    wait_chunk(gg * 16);
+                    if (pmask && waited1) flush_pending();
+                }
                 if constexpr (kF16) {
                     tmem_ld16h_issue(taddr_lane + uint32_t(gg * 16), f);
                     tmem_ld_wait8(f);
@@ -497,30 +531,8 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     if (kBoth) dn_w = __shfl_sync(0xFFFFFFFFu, H[D][lw], src_dn);
                 }
                 if (!valid) continue;
-                if (kTrack || !update) {
-                    if (energy) {
-                        // E' = -(jm/2) sum_i sigma_i(t) (D_i + h_i/jm): sigma(t) is H[0]
-                        const uint32_t sw = H[0][lw];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int j = half * 8 + q;
-                            const int i = i0 + 2 * q;
-                            if constexpr (kF16) {
-                                // D + h/jm as an FP16 pair (exact: |D_i| + |h_i/jm| <= 2048 on this
-                                // variant; zero beyond N), sign-flipped by sigma, added into FP32
-                                const uint32_t hp = reinterpret_cast<const uint32_t *>(sh)[i >> 1];
-                                const uint32_t y2 = h2u(__hadd2(u2h(f[q]), u2h(hp))) ^ ((sw << j) & kSignPair);
-                                esum = add_h2_to_f32(esum, y2);
-                            } else {
-                                const float y0 = __uint_as_float(f[2 * q]) + (i < a.N ? sh[i] : 0.f);
-                                const float y1 = __uint_as_float(f[2 * q + 1]) + (i + 1 < a.N ? sh[i + 1] : 0.f);
-                                const uint32_t sl = (sw << (16 + j)) & 0x80000000u;
-                                const uint32_t shi = (sw << j) & 0x80000000u;
-                                esum += __uint_as_float(__float_as_uint(y0) ^ sl);
-                                esum += __uint_as_float(__float_as_uint(y1) ^ shi);
-                            }
-                        }
-                    }
+                if constexpr (kTrack) {
+                    if (energy) esum = energy_add(f, H[0][lw], half, i0, esum);
                     if (!update) continue;
                 }
                 if (!kShfl && (half == 0 || g == 0)) {
@@ -579,7 +591,8 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     for (int q = 0; q < 8; ++q) sgn[q] = isn[q] & kSignPair;
                     b = fp8_bytes(sgn);
                 }
-                if (i0 + 16 > a.N) b = mask_tail(b, i0, a.N);
+                // (spins N .. N16 - 1 of a ragged granule may hold +-1 here: B is zero in
+                // those K columns, so they add nothing to D)
                 if (g < 4 && p.nchunk > 1 && !waited1) {
                     pend[g < 4 ? g : 0] = b;
                     pmask |= 1u << g;
@@ -639,6 +652,47 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
             }
         }
         bar_sync(1, kThreads);
+    }
+
+    // --------------------------------------- final energy (untracked variants)
+    if constexpr (!kTrack) {
+        if (need_final && !*abort_flag) {
+            const uint32_t parity = uint32_t(a.cycles) & 1u;
+            if (mma_warp) {
+                tc_fence_after();
+                if (lane == 0) issue_mmas();
+                __syncwarp();
+            }
+            bool waited0 = false, waited1 = false;
+            float esum = 0.f;
+#pragma unroll
+            for (int g = 0; g < kMaxG; ++g) {
+                const int gg = gran_of(g);
+                if (gg >= p.G) break;
+                const bool ch1 = p.nchunk > 1 && gg * 16 >= p.crow[0];
+                if (!(ch1 ? waited1 : waited0)) {
+                    if (!mbar_wait(&bars[ch1 ? 1 : 0], parity)) {
+                        *abort_flag = 1;
+                        atomicExch(p.err, 1);
+                    }
+                    (ch1 ? waited1 : waited0) = true;
+                    tc_fence_after();
+                }
+                uint32_t f[kF16 ? 8 : 16];
+                if constexpr (kF16) {
+                    tmem_ld16h_issue(taddr_lane + uint32_t(gg * 16), f);
+                    tmem_ld_wait8(f);
+                } else {
+                    tmem_ld16_issue(taddr_lane + uint32_t(gg * 16), f);
+                    tmem_ld_wait(f);
+                }
+                if (valid) esum = energy_add(f, H[0][g >> 1], g & 1, gg * 16, esum);
+            }
+            if (valid) atomicAdd(&eacc[c], static_cast<unsigned long long>(static_cast<long long>(esum)));
+            tc_fence_before();
+            bar_sync(2, kThreads);
+            if (valid && part == 0) e_fin = -(int64_t(p.jm) * static_cast<long long>(eacc[c])) / 2;
+        }
     }
 
     // ---------------------------------------------------------------- outputs
