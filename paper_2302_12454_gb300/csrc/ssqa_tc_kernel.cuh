@@ -530,9 +530,11 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     up_w = __shfl_sync(0xFFFFFFFFu, H[D][lw], src_up);
                     if (kBoth) dn_w = __shfl_sync(0xFFFFFFFFu, H[D][lw], src_dn);
                 }
-                if (!valid) continue;
+                // (lanes of columns beyond the last trial compute on zeros and write only
+                // their own, unused rows of A; a whole trial is valid or not, so no valid
+                // lane reads them)
                 if constexpr (kTrack) {
-                    if (energy) esum = energy_add(f, H[0][lw], half, i0, esum);
+                    if (energy && valid) esum = energy_add(f, H[0][lw], half, i0, esum);
                     if (!update) continue;
                 }
                 if (!kShfl && (half == 0 || g == 0)) {
