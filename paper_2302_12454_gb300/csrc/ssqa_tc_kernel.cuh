@@ -469,18 +469,13 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
             const uint32_t LO2 = h2u(__floats2half2_rn(p.bias - i0f, p.bias - i0f));
             const uint32_t HI2 = h2u(__floats2half2_rn(p.bias + i0f - float(a.alpha), p.bias + i0f - float(a.alpha)));
             const uint32_t TOP2 = h2u(__floats2half2_rn(p.bias + i0f, p.bias + i0f));
-            bool waited0 = false, waited1 = false;
-            auto wait_chunk = [&](int i0) {
-                const int ch = (p.nchunk > 1 && i0 >= p.crow[0]) ? 1 : 0;
-                bool &w = ch ? waited1 : waited0;
-                if (!w) {
-                    if (!mbar_wait(&bars[ch], parity)) {
-                        *abort_flag = 1;
-                        atomicExch(p.err, 1);
-                    }
-                    w = true;
-                    tc_fence_after();
+            bool waited1 = false;
+            auto wait_bar = [&](int ch) {
+                if (!mbar_wait(&bars[ch], parity)) {
+                    *abort_flag = 1;
+                    atomicExch(p.err, 1);
                 }
+                tc_fence_after();
             };
             // noise words of this cycle: computed while the tensor cores run
             Philox4 ph;
@@ -492,6 +487,8 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
             for (int q = 0; q < kMaxW; ++q) newW[q] = 0u;
             float esum = 0.f;
             uint32_t up_w = 0, dn_w = 0;
+            // the first chunk completes first: await it once (threads with granules)
+            if (gran_of(0) < p.G) wait_bar(0);
             // The second chunk's MMAs read every spin of A, so sigma(t+1) bytes of
             // granules finished before they complete wait here (only the first
             // four granule slots can lie in the first chunk, which is < 256 spins).
@@ -510,10 +507,11 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 if (gg >= p.G) break;
                 uint32_t f[kF16 ? 8 : 16];  // FP32 values, or FP16 pairs (kF16)
                 // Slots >= 4 hold granules >= 16 (spins >= 256 >= the first chunk's end), so
-                // with two chunks the second is awaited by slot 4; with one, by slot 0.
-                if (g <= 4) {
-                    wait_chunk(gg * 16);
-                    if (pmask && waited1) flush_pending();
+                // the second chunk is awaited by slot 4 at the latest.
+                if (g <= 4 && p.nchunk > 1 && !waited1 && gg * 16 >= p.crow[0]) {
+                    wait_bar(1);
+                    waited1 = true;
+                    flush_pending();
                 }
                 if constexpr (kF16) {
                     tmem_ld16h_issue(taddr_lane + uint32_t(gg * 16), f);
@@ -603,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 }
             }
             if (pmask) {
-                wait_chunk(p.crow[0]);
+                if (!waited1) wait_bar(1);
                 flush_pending();
             }
             if (energy && valid) atomicAdd(&eacc[c], static_cast<unsigned long long>(
