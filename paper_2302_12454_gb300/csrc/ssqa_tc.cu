@@ -106,7 +106,7 @@ bool plan(const TcImage &img, const AnnealArgs &a, Layout *L, std::string *why) 
     L->smem_e = off;
     off += kCT * 8;
     L->smem_bar = off;
-    off += 64;
+    off += 64 + 32 * 16;  // barriers, TMEM address, abort flag; the issuing warp's noise words
     L->total = off + 1024;  // alignment slack
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);

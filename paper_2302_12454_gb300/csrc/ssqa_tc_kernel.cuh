@@ -98,6 +98,9 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
@@ -238,6 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + p.smem_bar);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3);
+    uint4 *xph = reinterpret_cast<uint4 *>(bars + 8);  // [32] noise words of the issuing warp's lanes
 
     const AnnealArgs &a = p.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -477,11 +481,37 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 }
                 tc_fence_after();
             };
-            // noise words of this cycle: computed while the tensor cores run
+            // noise words of this cycle, computed while the tensor cores run.  The
+            // issuing warp is busy issuing then, so warp 11 (same columns, part 2)
+            // also computes its words (counter 3) and passes them on in xph.
             Philox4 ph;
             ph.x[0] = ph.x[1] = ph.x[2] = ph.x[3] = 0;
-            if (update && valid)
-                ph = philox4x32_10(uint32_t(part), uint32_t(k), trial_g, uint32_t(t), key0, key1);
+            {
+                const bool helper = warp == kEpiWarps - 5;
+                const int nph = mma_warp ? 0 : (helper ? 2 : 1);
+#pragma unroll 1
+                for (int r = 0; r < nph; ++r) {
+                    Philox4 px;
+                    px.x[0] = px.x[1] = px.x[2] = px.x[3] = 0;
+                    if (update && valid)
+                        px = philox4x32_10(uint32_t(r ? part + 1 : part), uint32_t(k), trial_g, uint32_t(t), key0, key1);
+                    if (r == 0)
+                        ph = px;
+                    else
+                        xph[lane] = make_uint4(px.x[0], px.x[1], px.x[2], px.x[3]);
+                }
+                if (helper) {
+                    __threadfence_block();
+                    bar_arrive(3, 64);
+                } else if (mma_warp) {
+                    bar_sync(3, 64);
+                    const uint4 v = xph[lane];
+                    ph.x[0] = v.x;
+                    ph.x[1] = v.y;
+                    ph.x[2] = v.z;
+                    ph.x[3] = v.w;
+                }
+            }
             uint32_t newW[kMaxW];
 #pragma unroll
             for (int q = 0; q < kMaxW; ++q) newW[q] = 0u;
