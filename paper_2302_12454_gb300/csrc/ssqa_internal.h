@@ -36,7 +36,7 @@ struct TcImage {
     int32_t N16 = 0;          // N rounded up to 16
     int32_t nh = 0;           // number of h digit columns
     int32_t Kp = 0;           // K extent (multiple of 32)
-    int32_t nchunk = 0;       // MMA N-chunks (<= 2)
+    int32_t nchunk = 0;       // MMA N-chunks (<= 2): rows [0, chunk_rows[0]) then the rest
     int32_t chunk_rows[2] = {0, 0};
     int32_t Brows = 0;        // sum of chunk rows
     std::vector<uint8_t> b;   // B image, Brows * Kp bytes

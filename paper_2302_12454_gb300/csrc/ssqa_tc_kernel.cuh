@@ -7,19 +7,26 @@
 //
 //   shared memory  A = sigma(t) as FP8 E4M3 (+1/-1), 128 x Kp, rewritten each
 //                  cycle by the epilogue; B = J / jm and the h digits, read
-//                  once from global memory; one word-per-32-spins bit slot
+//                  once from global memory; h / jm for the energy; with the
+//                  shared-memory exchange, one word-per-32-spins bit slot
 //                  with sigma(t - d) of every column for the replica term.
-//   tensor memory  D[c][i] = sum_j sigma_{j,c}(t) J_ij / jm + h_i / jm, FP32,
-//                  produced by tcgen05.mma kind::f8f6f4 (exact: every operand
-//                  is a small integer and every partial sum is below 2^14).
-//   registers      the integral counters Is (Eq. 6b) as packed half2, and the
-//                  thread's own spin history as bit words.
+//   tensor memory  D[c][i] = sum_j sigma_{j,c}(t) J_ij / jm + h_i / jm, FP32
+//                  or FP16, produced by tcgen05.mma kind::f8f6f4 in two
+//                  N-chunks of rows (exact: every operand is a small integer
+//                  and every partial sum is below 2^14; FP16 only where every
+//                  partial sum, and D + h / jm, is at most 2048).
+//   registers      the integral counters Is (Eq. 6b) as biased bytes or
+//                  packed half2, and the thread's own spin history as bit
+//                  words.
 //
 // Warp roles: all 16 warps run the epilogue (warp w reads TMEM lanes
-// 32*(w%4).., i.e. columns, and a quarter (w/4) of the spins); warp 0 also
+// 32*(w%4).., i.e. columns, and a quarter (w/4) of the spins); warp 15 also
 // allocates TMEM and its lane 0 issues the MMAs.  Per cycle:
-//   MMA(sigma(t)) -> commit -> epilogue: D -> local field (Eq. 6a) ->
-//   counter (Eq. 6b) -> sign (Eq. 6c) -> sigma(t+1) into A -> barrier.
+//   MMA(sigma(t)) -> commit per chunk -> epilogue: D -> local field (Eq. 6a)
+//   -> counter (Eq. 6b) -> sign (Eq. 6c) -> sigma(t+1) into A -> barrier;
+// the first chunk's epilogue runs while the second chunk's MMAs do.  The
+// cycle loop is kept small (the final energy of untracked runs is a separate
+// pass after it): at 16 warps x 128 registers its speed follows its code size.
 // Epilogue arithmetic is exact in FP16: the local field is an integer, and
 // any value above 2048 in magnitude (the only ones FP16 rounds) saturates
 // the counter in the same direction as the exact value, because the host
