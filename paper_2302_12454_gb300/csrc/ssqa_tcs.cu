@@ -1,8 +1,8 @@
 // Streamed tensor-core path of SSQA for sm_103a, for instances whose
 // operands do not fit in one SM (N > 400).
 //
-// A CTA owns 128 spin columns (whole trials, as in the resident kernel) and a
-// share of the spin chunks (256 spins each) of the field product
+// A CTA owns two groups of 128 spin columns (whole trials, as in the resident
+// kernel) and a share of the spin chunks (256 spins each) of the field product
 //   D[c][i] = sum_j sigma_{j,c}(t) J_ij / jm + h_i / jm     (Eq. 6a, exact FP8)
 // A thread-block cluster of CS CTAs covers all chunks of one column group;
 // chunk ch belongs to cluster rank ch mod CS.  Per cycle:
@@ -40,7 +40,8 @@ using namespace tc;
 constexpr int kStages = 12;
 constexpr int kABytes = 128 * 32;   // one K-block of A
 constexpr int kBBytes = 256 * 32;   // one K-block of a B chunk
-constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kStageBytes = 2 * kABytes + kBBytes;  // dual mode: A of both column groups, one B block
+constexpr int kStageBytes1 = kABytes + kBBytes;     // single mode
 constexpr int kEpi = 8;             // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kThr = (2 + kEpi) * 32;
 
@@ -55,6 +56,7 @@ struct SParams {
     int32_t *bcyc;             // [cols]
     int *err;
     int32_t N16, KB, NCH, L, CS, Tb, jm, last_rows;
+    int32_t dual;           // a CTA serves two column groups (one accumulator buffer each)
     uint32_t NR2, JM2;
     float bias;
     int32_t i0_levels, i0_mult, i0_tau;
@@ -90,12 +92,16 @@ __device__ __forceinline__ uint32_t blk_off(int r, int k) {
 __device__ __forceinline__ int64_t slot_of(int64_t t, int32_t L) { return ((t % L) + L) % L; }
 
 // ------------------------------------------------------------------- kernel
-template <bool kTrack>
+template <bool kTrack, bool kDual>
 __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant__ SParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *ring = sm;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kStages * kStageBytes);
+    // stage = A (one or two groups) then B; single mode keeps the ring small,
+    // leaving more of the SM's memory to L1 for the epilogue's global state
+    constexpr int sbytes = kDual ? kStageBytes : kStageBytes1;
+    constexpr int boff = kDual ? 2 * kABytes : kABytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kStages * sbytes);
     uint64_t *empty = full + kStages;
     uint64_t *tfull = empty + kStages;   // [2]
     uint64_t *tempty = tfull + 2;        // [2]
@@ -105,16 +111,19 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
     const AnnealArgs &a = p.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rank = int(cluster_rank());
-    const int64_t grp = blockIdx.x / p.CS;
-    const int64_t trial0 = grp * p.Tb;
-    const int ntr = int(a.trials - trial0 < p.Tb ? a.trials - trial0 : p.Tb);
-    const int vcols = ntr * a.R;
-    const int64_t col0 = trial0 * a.R;
+    // Dual mode: column groups 2 pg and 2 pg + 1 (the second may not exist),
+    // whose MMAs share each B block, one TMEM accumulator per group.  Single
+    // mode: one group, its accumulator double-buffered across chunks so that
+    // a chunk's epilogue overlaps the next chunk's MMAs.
+    const int64_t ngroups = (int64_t(a.trials) + p.Tb - 1) / p.Tb;
+    const int64_t grp0 = (kDual ? 2 : 1) * int64_t(blockIdx.x / p.CS);
+    const int ng = kDual && grp0 + 1 < ngroups ? 2 : 1;
     const bool need_final = a.e_final != nullptr || kTrack;
     const int iters = a.cycles + (need_final ? 1 : 0);
     const int nmine = (p.NCH - rank + p.CS - 1) / p.CS;  // chunks rank, rank + CS, ...
     const int64_t cols = int64_t(a.trials) * a.R;
-    uint8_t *Ag = p.A + grp * int64_t(p.L) * p.KB * kABytes;
+    const int64_t slot_stride = int64_t(p.L) * p.KB * kABytes;  // one group's operand slots
+    uint8_t *Ag0 = p.A + grp0 * slot_stride;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -147,18 +156,24 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
     uint32_t mt_ph = 3u;   // MMA: tmem-empty parity per buffer (bit b)
     uint32_t et_ph = 0u;   // epilogue: tmem-full parity per buffer (bit b)
 
-    // epilogue identity: TMEM lane quadrant qd (column c), part 0 / 1 of the words
+    // epilogue identity: TMEM lane quadrant qd (column c of each group), part
+    // 0 / 1 of the words; group gi's accumulator is at TMEM column 256 gi
     const int ew = warp - 2;
     const int qd = warp & 3, part = ew >> 2;
     const int c = qd * 32 + lane;
-    const bool valid = warp >= 2 && c < vcols;
-    const int lt = valid ? c / a.R : 0, k = valid ? c % a.R : 0;
-    const uint32_t trial_g = a.trial_offset + uint32_t(trial0 + lt);
+    auto vcols_of = [&](int gi) -> int {
+        const int64_t tr0 = (grp0 + gi) * p.Tb;
+        return int((a.trials - tr0 < p.Tb ? a.trials - tr0 : p.Tb) * a.R);
+    };
+    const bool valid0 = warp >= 2 && c < vcols_of(0);
+    const bool valid1 = kDual && warp >= 2 && ng > 1 && c < vcols_of(1);
+    const int lt = valid0 ? c / a.R : 0, k = valid0 ? c % a.R : 0;
     const int nb_up = lt * a.R + (k + 1) % a.R;
     const int nb_dn = lt * a.R + (k + a.R - 1) % a.R;
-    const int64_t gcol = col0 + c;
-    int64_t e_best = LLONG_MAX;
-    int32_t best_cycle = -1;
+    const int64_t gcol0 = grp0 * p.Tb * a.R + c;
+    const int64_t gcol1 = gcol0 + int64_t(p.Tb) * a.R;
+    int64_t e_best0 = LLONG_MAX, e_best1 = LLONG_MAX;
+    int32_t best_cycle0 = -1, best_cycle1 = -1;
 
     const int64_t period = int64_t(a.tau) * (a.beta + 1);
     int sub = int((int64_t(a.start_cycle) % period) % a.tau);
@@ -173,7 +188,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
         const int64_t t = int64_t(a.start_cycle) + it;
         const bool update = it < a.cycles;
         const bool energy = (kTrack && it > 0) || !update;
-        const uint8_t *Acur = Ag + slot_of(t, p.L) * p.KB * kABytes;
+        const int64_t cur_off = slot_of(t, p.L) * p.KB * kABytes;  // sigma(t) slot of a group
         if (*reinterpret_cast<volatile int *>(p.err)) abort_run = true;
         if (warp == 0) {
             // ---------------------------------------------------- producer
@@ -189,10 +204,14 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                             abort_run = true;
                             break;
                         }
-                        uint8_t *st = ring + ps * kStageBytes;
-                        mbar_expect_tx(&full[ps], kStageBytes);
-                        bulk_g2s(st, Acur + int64_t(kb) * kABytes, kABytes, &full[ps]);
-                        bulk_g2s(st + kABytes, Bc + int64_t(kb) * kBBytes, kBBytes, &full[ps]);
+                        // A of each group, then the B block both groups' MMAs share
+                        uint8_t *st = ring + ps * sbytes;
+                        mbar_expect_tx(&full[ps], uint32_t(ng * kABytes + kBBytes));
+                        bulk_g2s(st, Ag0 + cur_off + int64_t(kb) * kABytes, kABytes, &full[ps]);
+                        if (kDual && ng > 1)
+                            bulk_g2s(st + kABytes, Ag0 + slot_stride + cur_off + int64_t(kb) * kABytes, kABytes,
+                                     &full[ps]);
+                        bulk_g2s(st + boff, Bc + int64_t(kb) * kBBytes, kBBytes, &full[ps]);
                         ++nis;
                         if (++ps == kStages) {
                             ps = 0;
@@ -207,10 +226,11 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
             if (lane == 0 && !abort_run) {
                 for (int m = 0; m < nmine && !abort_run; ++m) {
                     const int ch = rank + m * p.CS;
-                    const int b = m & 1;
+                    const int b = kDual ? 0 : (m & 1);  // accumulator buffer
                     const int rows = ch == p.NCH - 1 ? p.last_rows : 256;
                     const uint32_t idesc = (1u << 4) | (uint32_t(rows >> 3) << 17) | (uint32_t(128 >> 4) << 24);
                     if (m > 0 && *reinterpret_cast<volatile int *>(p.err)) abort_run = true;
+                    // the epilogue has read this buffer's previous accumulators
                     if (abort_run || !mbar_wait(&tempty[b], (mt_ph >> b) & 1u)) {
                         if (!abort_run) atomicExch(p.err, 1);
                         abort_run = true;
@@ -225,11 +245,12 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t st = smem_u32(ring + ms * kStageBytes);
-                        const uint64_t ad = smem_desc(st, 128u, 256u);
-                        const uint64_t bd = smem_desc(st + kABytes, 128u, 256u);
-                        mma_f8f6f4(tmem + uint32_t(b * 256), ad, bd, idesc, kb > 0 ? 1u : 0u);
-                        mma_commit(&empty[ms]);  // frees the stage when this MMA completes
+                        const uint32_t st = smem_u32(ring + ms * sbytes);
+                        const uint64_t bd = smem_desc(st + uint32_t(boff), 128u, 256u);
+                        mma_f8f6f4(tmem + uint32_t(b * 256), smem_desc(st, 128u, 256u), bd, idesc, kb > 0 ? 1u : 0u);
+                        if (kDual && ng > 1)
+                            mma_f8f6f4(tmem + 256u, smem_desc(st + kABytes, 128u, 256u), bd, idesc, kb > 0 ? 1u : 0u);
+                        mma_commit(&empty[ms]);  // frees the stage when these MMAs complete
                         if (++ms == kStages) {
                             ms = 0;
                             mph ^= 1;
@@ -249,12 +270,24 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
             const uint32_t LO2 = h2u(__floats2half2_rn(p.bias - i0f, p.bias - i0f));
             const uint32_t HI2 = h2u(__floats2half2_rn(p.bias + i0f - float(a.alpha), p.bias + i0f - float(a.alpha)));
             const uint32_t TOP2 = h2u(__floats2half2_rn(p.bias + i0f, p.bias + i0f));
-            const uint8_t *Aold = Ag + slot_of(t - a.delay, p.L) * p.KB * kABytes;
-            uint8_t *Anext = Ag + slot_of(t + 1, p.L) * p.KB * kABytes;
-            long long esum = 0;
+            const int64_t old_off = slot_of(t - a.delay, p.L) * p.KB * kABytes;
+            const int64_t next_off = slot_of(t + 1, p.L) * p.KB * kABytes;
+            long long esum0 = 0, esum1 = 0;
             for (int m = 0; m < nmine && !abort_run; ++m) {
                 const int ch = rank + m * p.CS;
-                const int b = m & 1;
+                const int b = kDual ? 0 : (m & 1);
+#pragma unroll 1
+                for (int gi = 0; gi < (kDual ? ng : 1); ++gi) {
+                // group gi: its columns, operand slots, counters and noise
+                const bool valid = gi ? valid1 : valid0;
+                const int64_t trial0 = (grp0 + gi) * p.Tb;
+                const uint32_t trial_g = a.trial_offset + uint32_t(trial0 + lt);
+                const int64_t gcol = trial0 * a.R + c;
+                uint8_t *Ag = Ag0 + gi * slot_stride;
+                const uint8_t *Acur = Ag + cur_off;
+                const uint8_t *Aold = Ag + old_off;
+                uint8_t *Anext = Ag + next_off;
+                long long esum = 0;
                 // This thread's words of the chunk: 8 ch + 2 part + {0, 4, 1, 5}.
                 // Words 8 ch + 2 part and + 4 share one Philox call (same counter),
                 // as do + 1 and + 5; both calls are made before the MMAs are awaited.
@@ -272,14 +305,16 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     nq2 = odd ? ph1.x[2] : ph1.x[0];
                     nq3 = odd ? ph1.x[3] : ph1.x[1];
                 }
-                const bool ok = mbar_wait(&tfull[b], (et_ph >> b) & 1u);
-                if (__any_sync(0xffffffffu, !ok)) {
-                    if (lane == 0) atomicExch(p.err, 1);
-                    abort_run = true;
-                    break;
+                if (gi == 0) {  // the chunk's accumulators (of both groups)
+                    const bool ok = mbar_wait(&tfull[b], (et_ph >> b) & 1u);
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        if (lane == 0) atomicExch(p.err, 1);
+                        abort_run = true;
+                        break;
+                    }
+                    et_ph ^= 1u << b;
+                    tc_fence_after();
                 }
-                et_ph ^= 1u << b;
-                tc_fence_after();
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {
                     const int w = wbase + 4 * (q & 1) + (q >> 1);
@@ -290,7 +325,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                         if (i0 >= p.N16) continue;  // warp-uniform
                         uint32_t f[16];
                         __syncwarp();
-                        tmem_ld16_issue(tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * 256 + (i0 - 256 * ch)), f);
+                        tmem_ld16_issue(tmem + (uint32_t(qd * 32) << 16) + uint32_t((b + gi) * 256 + (i0 - 256 * ch)), f);
                         tmem_ld_wait(f);
                         if (!valid) continue;
                         const int kb = i0 >> 5;
@@ -359,25 +394,39 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                         *reinterpret_cast<uint4 *>(Anext + int64_t(kb) * kABytes + ob) = bo;
                     }
                 }
+                if (gi)
+                    esum1 += esum;
+                else
+                    esum0 += esum;
+                }
+                if (abort_run) break;
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
             }
-            if (energy && valid && !abort_run)
-                atomicAdd(&p.eacc[(it & 1) * cols + gcol], static_cast<unsigned long long>(esum));
+            if (energy && valid0 && !abort_run)
+                atomicAdd(&p.eacc[(it & 1) * cols + gcol0], static_cast<unsigned long long>(esum0));
+            if (energy && valid1 && !abort_run)
+                atomicAdd(&p.eacc[(it & 1) * cols + gcol1], static_cast<unsigned long long>(esum1));
             fence_async_global();
         }
         // ------------------------------------------------------ cycle end
         cluster_sync();
-        if (energy && rank == 0 && valid && part == 0) {
-            const long long s = static_cast<long long>(atomicExch(&p.eacc[(it & 1) * cols + gcol], 0ull));
-            const int64_t E = -(int64_t(p.jm) * s) / 2;
-            if (kTrack && it > 0 && E < e_best) {
-                e_best = E;
-                best_cycle = int32_t(t);
+        if (energy && rank == 0 && part == 0) {
+#pragma unroll
+            for (int gi = 0; gi < 2; ++gi) {
+                if (!(gi ? valid1 : valid0)) continue;
+                const int64_t gcol = gi ? gcol1 : gcol0;
+                const long long s = static_cast<long long>(atomicExch(&p.eacc[(it & 1) * cols + gcol], 0ull));
+                const int64_t E = -(int64_t(p.jm) * s) / 2;
+                int64_t &eb = gi ? e_best1 : e_best0;
+                if (kTrack && it > 0 && E < eb) {
+                    eb = E;
+                    (gi ? best_cycle1 : best_cycle0) = int32_t(t);
+                }
+                if (kTrack && it > 0 && a.e_trace) a.e_trace[int64_t(it - 1) * cols + gcol] = E;
+                if (!update && p.efin) p.efin[gcol] = E;
             }
-            if (kTrack && it > 0 && a.e_trace) a.e_trace[int64_t(it - 1) * cols + gcol] = E;
-            if (!update && p.efin) p.efin[gcol] = E;
         }
         if (++sub == a.tau) {
             sub = 0;
@@ -393,9 +442,15 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
             }
         }
     }
-    if (kTrack && rank == 0 && valid && part == 0) {
-        p.ebest[gcol] = e_best;
-        p.bcyc[gcol] = best_cycle;
+    if (kTrack && rank == 0 && part == 0) {
+        if (valid0) {
+            p.ebest[gcol0] = e_best0;
+            p.bcyc[gcol0] = best_cycle0;
+        }
+        if (valid1) {
+            p.ebest[gcol1] = e_best1;
+            p.bcyc[gcol1] = best_cycle1;
+        }
     }
     // Drain before exit: the producer waits (bounded) for its last copy into
     // every stage, the MMA thread for all MMAs it issued.
@@ -599,7 +654,13 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int CS = int(nsm / (groups > 0 ? groups : 1));
+    // Two column groups per CTA cut the operand bytes per MAC by a third, but
+    // leave a chunk's epilogue unhidden: it pays off for long chunks (SK
+    // N = 8192, 256 K-blocks: 1.5x) and not for short ones (N = 2500, 80
+    // K-blocks: 6 % slower).
+    p.dual = img.KB >= 160 ? 1 : 0;
+    const int64_t pairs = p.dual ? (groups + 1) / 2 : groups;  // CTAs per cluster rank
+    int CS = int(nsm / (pairs > 0 ? pairs : 1));
     if (CS > 8) CS = 8;
     if (CS > p.NCH) CS = p.NCH;
     if (CS < 1) CS = 1;
@@ -630,8 +691,9 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
             return fail(SSQA_ERR_UNSUPPORTED, "streamed tensor path: resumed counters outside -128..127");
         }
     }
-    void (*fn)(SParams) = a.track_best ? ssqa_tcs_kernel<true> : ssqa_tcs_kernel<false>;
-    const int smem = kStages * kStageBytes + 1024 + 512;  // ring + alignment + barriers
+    void (*fn)(SParams) = a.track_best ? (p.dual ? ssqa_tcs_kernel<true, true> : ssqa_tcs_kernel<true, false>)
+                                       : (p.dual ? ssqa_tcs_kernel<false, true> : ssqa_tcs_kernel<false, false>);
+    const int smem = kStages * (p.dual ? kStageBytes : kStageBytes1) + 1024 + 512;  // ring + alignment + barriers
     configure_once(fn, smem);
     cudaLaunchConfig_t cfg{};
     cfg.blockDim = dim3(kThr, 1, 1);
@@ -646,13 +708,13 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
     // the largest cluster (<= CS) that the device can place at least once
     for (; CS > 1; --CS) {
         int nclus = 0;
-        cfg.gridDim = dim3(unsigned(groups * CS), 1, 1);
+        cfg.gridDim = dim3(unsigned(pairs * CS), 1, 1);
         attr[0].val.clusterDim.x = unsigned(CS);
         if (cudaOccupancyMaxActiveClusters(&nclus, fn, &cfg) == cudaSuccess && nclus > 0) break;
         cudaGetLastError();
     }
     p.CS = CS;
-    cfg.gridDim = dim3(unsigned(groups * CS), 1, 1);
+    cfg.gridDim = dim3(unsigned(pairs * CS), 1, 1);
     attr[0].val.clusterDim.x = unsigned(CS);
     if (!e) e = cudaLaunchKernelEx(&cfg, fn, p);
     if (!e) {

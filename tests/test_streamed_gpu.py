@@ -192,3 +192,18 @@ def test_streamed_cluster_shapes(case):
         o = O.anneal(h, J, trial_offset=tr, track_best=True, **okw)
         for k in ("sigma", "Is", "E_final", "E_best", "best_cycle"):
             np.testing.assert_array_equal(g[k][tr:tr + 1], o[k], err_msg=k)
+
+
+def test_two_column_groups_per_cta():
+    """From 160 K-blocks per chunk (N = 5152 here) a CTA serves two groups of
+    128 columns whose MMAs share each B block.  R = 32 and 10 trials make
+    three groups (4 + 4 + 2 trials): one CTA pair with both groups, one with
+    a single, partial group.  A trial of each group against the oracle."""
+    N, R, trials, cycles = 5152, 32, 10, 4
+    I = sk(N, 41, hscale=12)
+    h, J, _ = I.export()
+    g = S.anneal(I, R=R, cycles=cycles, trials=trials, seed=43, tau=2, algo=ST, track_best=True)
+    for tr in (1, 6, 9):
+        o = O.anneal(h, J, R=R, cycles=cycles, trials=1, seed=43, tau=2, trial_offset=tr, track_best=True)
+        for k in ("sigma", "Is", "E_final", "E_best", "best_cycle"):
+            np.testing.assert_array_equal(g[k][tr], o[k][0], err_msg=f"{k} trial {tr}")
