@@ -76,6 +76,22 @@ def test_dense_instance_roundtrip_and_checks():
         S.Ising.dense(bad, h)
 
 
+def test_dense_instance_symmetry_checked_in_every_tile():
+    """The symmetry check runs over 32 x 32 tiles; a single asymmetric pair
+    anywhere (corner tiles, the ragged last tile of N = 77, either triangle)
+    is rejected, and the symmetric instance is accepted."""
+    N = 77
+    J = W.sk_couplings(N, 9)
+    h = np.zeros(N, np.int32)
+    S.Ising.dense(J, h)
+    for i, j in ((76, 0), (0, 76), (40, 70), (33, 65), (31, 32), (64, 76), (75, 74)):
+        bad = J.copy()
+        bad[i, j] = -bad[i, j] if bad[i, j] else 12
+        with pytest.raises(S.SSQAError) as e:
+            S.Ising.dense(bad, h)
+        assert e.value.code == S.ERR_INVALID_ARG, (i, j)
+
+
 def test_gi_builder_rejects_bad_graphs():
     a = np.zeros((4, 4), np.uint8)
     a[0, 1] = 1  # asymmetric
