@@ -1,23 +1,29 @@
 // Streamed tensor-core path of SSQA for sm_103a, for instances whose
 // operands do not fit in one SM (N > 400).
 //
-// A CTA owns two groups of 128 spin columns (whole trials, as in the resident
-// kernel) and a share of the spin chunks (256 spins each) of the field product
+// A CTA owns one group of 128 spin columns (whole trials, as in the resident
+// kernel), or two groups in dual mode, and a share of the spin chunks (256
+// spins each) of the field product
 //   D[c][i] = sum_j sigma_{j,c}(t) J_ij / jm + h_i / jm     (Eq. 6a, exact FP8)
-// A thread-block cluster of CS CTAs covers all chunks of one column group;
+// A thread-block cluster of CS CTAs covers all chunks of its column group(s);
 // chunk ch belongs to cluster rank ch mod CS.  Per cycle:
 //   producer warp  streams, for each owned chunk, the K-blocks of A (sigma(t)
-//                  of the 128 columns, 4 KB) and B (J rows of the chunk, 8 KB)
-//                  from L2 into a 12-stage shared-memory ring (bulk async
-//                  copies completing on mbarriers);
-//   MMA warp       issues one tcgen05.mma kind::f8f6f4 (M 128, N <= 256, K 32)
-//                  per stage into one of two TMEM accumulators;
-//   8 epilogue warps turn a finished accumulator into sigma(t+1) of the chunk
+//                  of 128 columns, 4 KB per group) and B (J rows of the chunk,
+//                  8 KB) from L2 into a 12-stage shared-memory ring (bulk
+//                  async copies completing on mbarriers);
+//   MMA warp       issues per stage one tcgen05.mma kind::f8f6f4 (M 128,
+//                  N <= 256, K 32) per group, all groups on the same B block;
+//   8 epilogue warps turn finished accumulators into sigma(t+1) of the chunk
 //                  (Eq. 6a-6c, the same packed-half2 arithmetic as the resident
-//                  kernel) while the next chunk's MMAs run;
+//                  kernel): in single mode while the next chunk's MMAs run
+//                  into the other of two TMEM buffers, in dual mode (one
+//                  buffer per group) before them;
 // and a cluster barrier closes the cycle.  sigma lives in L2 as FP8 operand
 // blocks, one slot per history level (the replica term reads the ring
 // neighbour's sigma(t - d) from its slot), and the counters as bytes Is + 128.
+// Dual mode carries a third fewer operand bytes per MAC; the host takes it
+// for chunks of at least 160 K-blocks, where the MMAs of a chunk outlast its
+// epilogue by far.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -97,8 +103,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *ring = sm;
-    // stage = A (one or two groups) then B; single mode keeps the ring small,
-    // leaving more of the SM's memory to L1 for the epilogue's global state
+    // stage = A (one block per group) then the B block
     constexpr int sbytes = kDual ? kStageBytes : kStageBytes1;
     constexpr int boff = kDual ? 2 * kABytes : kABytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + kStages * sbytes);
@@ -157,7 +162,8 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
     uint32_t et_ph = 0u;   // epilogue: tmem-full parity per buffer (bit b)
 
     // epilogue identity: TMEM lane quadrant qd (column c of each group), part
-    // 0 / 1 of the words; group gi's accumulator is at TMEM column 256 gi
+    // 0 / 1 of the words; accumulators at TMEM column 256 gi (dual mode,
+    // group gi) or 256 (m & 1) (single mode, the CTA's m-th chunk)
     const int ew = warp - 2;
     const int qd = warp & 3, part = ew >> 2;
     const int c = qd * 32 + lane;
