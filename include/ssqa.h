@@ -221,18 +221,40 @@ typedef struct ssqa_result {
 int ssqa_anneal(const ssqa_ising *ising, const ssqa_params *params, ssqa_result *out,
                 void *cuda_stream);
 
+/* The kernel path ssqa_anneal takes for this instance and these parameters,
+ * decided on the host without running anything (no GPU needed).  Not in the
+ * paper: it exposes the library's choice between its exact paths for Eq. 6
+ * (the resident and streamed tensor-core kernels, whose FP8 field product is
+ * exact only while every partial sum of J sigma + h stays an integer within
+ * the accumulator's exact range, and the CUDA-core paths).
+ *   desc: if non-NULL and len > 0, receives a NUL-terminated one-line
+ *   description (truncated to len - 1 bytes): the path and, for the resident
+ *   kernel, its accumulator (FP16 when max_i (|h_i| + sum_j |J_ij|) / jm +
+ *   max_i |h_i| / jm <= 2048, else FP32 up to 2^14), counter format and
+ *   replica exchange.
+ * Returns SSQA_ALGO_TENSOR (resident kernel), SSQA_ALGO_STREAMED,
+ * SSQA_ALGO_DELTA or SSQA_ALGO_PLAIN; or SSQA_ERR_INVALID_ARG (as for
+ * ssqa_anneal) or SSQA_ERR_UNSUPPORTED (a forced tensor path cannot take the
+ * problem).  A resumed state whose counters lie outside -128..127 is only seen
+ * at run time: AUTO then moves it from the streamed to the delta path. */
+int ssqa_plan(const ssqa_ising *ising, const ssqa_params *params, char *desc, size_t len);
+
 /* ssqa_anneal_noalloc -- the plain CUDA-core anneal (the computation of
  * ssqa_anneal with SSQA_ALGO_PLAIN) without any device-memory allocation.
  * The paper has no counterpart; this entry point exists for callers that
- * cannot allocate device memory: code running while a stream is captured
- * into a CUDA graph, plugins or real-time loops whose host framework owns
- * all device memory and forbids cudaMalloc after start-up, and deployments
- * that fix their device footprint at initialisation.
+ * cannot allocate device memory: plugins whose host framework owns all
+ * device memory and forbids cudaMalloc after start-up, real-time loops in
+ * which an allocation (which may synchronise the device) would break the
+ * timing, and deployments that fix their device footprint at
+ * initialisation.
  *   N: spins; J_padded: device, N rows of roundup(N, 16) bytes (row pitch
  *   roundup(N, 16), zero padded), symmetric J' with zero diagonal; h: device,
  *   N int32.  params: as for ssqa_anneal; flags must include
  *   SSQA_FLAG_DEVICE_PTRS (all `out` pointers are device pointers); algo is
  *   ignored.  The call only enqueues work on cuda_stream.
+ * Alignment: J_padded 16 bytes; h, is_state and best_cycle 4 bytes; e_final,
+ * e_best and e_trace 8 bytes (sigma and sigma_hist are bytes).  A misaligned
+ * pointer returns SSQA_ERR_INVALID_ARG before anything is launched.
  * Scratch: one fixed 16 MiB device array inside the library, held on every
  * GPU that loads the library until the process exits.  A problem needing
  * (delay + 2) * trials * R * roundup(N, 16) bytes plus 16 bytes per column
@@ -241,7 +263,10 @@ int ssqa_anneal(const ssqa_ising *ising, const ssqa_params *params, ssqa_result 
  * overlaps on the GPU (different streams, or different host threads on the
  * same device) race and must be serialised by the caller.
  * The first call on each device looks up the array's device address (once
- * per device); make that first call before any stream capture begins.
+ * per device, in the context current at that call, normally the device's
+ * primary context); make that first call before any stream capture begins.
+ * The cached address is not valid after cudaDeviceReset or in another
+ * context: use the entry point only in the context of its first call.
  * Never calls cudaMalloc, cudaFree or any allocating routine.
  * Errors: SSQA_ERR_INVALID_ARG, SSQA_ERR_DEVICE. */
 int ssqa_anneal_noalloc(int32_t N, const int8_t *J_padded, const int32_t *h, const ssqa_params *params,

@@ -71,6 +71,7 @@ def lib():
         L.ssqa_params_default.restype = None
         L.ssqa_anneal.argtypes = [vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
         L.ssqa_energy.argtypes = [vp, vp, i64, vp, u32, vp]
+        L.ssqa_plan.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_char_p, ctypes.c_size_t]
         L.ssqa_anneal_noalloc.argtypes = [i32, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
         L.ssqa_tts.argtypes = [ctypes.c_double] * 3
         L.ssqa_tts.restype = ctypes.c_double
@@ -252,6 +253,16 @@ def anneal_device(ising: Ising, params: Params, sigma, Is, e_final=None, hist=No
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     r = Result(_ptr(sigma), _ptr(hist), _ptr(Is), _ptr(e_final), _ptr(e_best), _ptr(best_cycle), _ptr(e_trace))
     _check(lib().ssqa_anneal(ising.handle, ctypes.byref(p), ctypes.byref(r), ctypes.c_void_p(handle)), "anneal")
+
+
+def plan(ising: Ising, *, R: int, cycles: int, trials: int, seed: int = 0, track_best: bool = False, **kw):
+    """(algo, description) of the kernel path ssqa_anneal would take (host only)."""
+    p = make_params(R=R, cycles=cycles, trials=trials, seed=seed, **kw)
+    if track_best:
+        p.flags |= FLAG_TRACK_BEST
+    buf = ctypes.create_string_buffer(512)
+    rc = _check(lib().ssqa_plan(ising.handle, ctypes.byref(p), buf, 512), "plan")
+    return rc, buf.value.decode()
 
 
 def energy(ising: Ising, sigma) -> np.ndarray:

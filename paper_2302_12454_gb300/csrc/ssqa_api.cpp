@@ -547,6 +547,77 @@ int validate(const ssqa_ising *I, const ssqa_params *p, const ssqa_result *r) {
     return SSQA_OK;
 }
 
+// Launch arguments of an anneal (instance pointers and buffers left empty).
+AnnealArgs make_args(const ssqa_ising *I, const ssqa_params *p) {
+    AnnealArgs a{};
+    a.N = I->N;
+    a.R = p->R;
+    a.trials = p->trials;
+    a.cycles = p->cycles;
+    a.I0 = p->I0;
+    a.alpha = p->alpha;
+    a.n_rnd = p->n_rnd;
+    a.jperp_min = p->jperp_min;
+    a.jperp_step = (p->jperp_max - p->jperp_min) / p->beta;
+    a.beta = p->beta;
+    a.tau = p->tau;
+    a.delay = p->delay;
+    a.both = p->coupling == SSQA_COUPLING_BOTH;
+    a.init_mode = p->init_mode;
+    a.start_cycle = p->start_cycle;
+    a.trial_offset = p->trial_offset;
+    a.seed = p->seed;
+    a.i0_max = p->i0_max;
+    a.i0_mult = p->i0_mult;
+    a.i0_tau = p->i0_tau;
+    a.track_best = p->flags & SSQA_FLAG_TRACK_BEST;
+    a.Np = (I->N + 15) / 16 * 16;
+    return a;
+}
+
+// The kernel path an anneal takes (host decision; no device work).  The
+// streamed path can still hand a resumed state whose counters do not fit a
+// byte back to the CUDA-core paths at run time (AUTO only).
+int choose_path(const ssqa_ising *I, const ssqa_params *p, const AnnealArgs &a, int *algo, std::string *desc) {
+    std::string why, why_s;
+    if (p->algo == SSQA_ALGO_PLAIN) {
+        *algo = SSQA_ALGO_PLAIN;
+        *desc = "plain CUDA-core path (dp4a), one launch per cycle";
+        return SSQA_OK;
+    }
+    if (p->algo == SSQA_ALGO_DELTA) {
+        *algo = SSQA_ALGO_DELTA;
+        *desc = "delta-field CUDA-core path";
+        return SSQA_OK;
+    }
+    bool use_tc = false, use_tcs = false;
+    if (p->algo == SSQA_ALGO_STREAMED) {
+        use_tcs = tcs_supported(I->tc, a, &why_s);
+        if (!use_tcs) return fail(SSQA_ERR_UNSUPPORTED, "streamed tensor path: " + why_s);
+    } else {
+        use_tc = tc_supported(I->tc, a, &why);
+        if (!use_tc) use_tcs = tcs_supported(I->tc, a, &why_s);
+        if (p->algo == SSQA_ALGO_TENSOR && !use_tc && !use_tcs)
+            return fail(SSQA_ERR_UNSUPPORTED, "tensor path: " + why + "; streamed tensor path: " + why_s);
+    }
+    if (use_tc) {
+        const TcVariant v = tc_variant(I->tc, a);
+        *algo = SSQA_ALGO_TENSOR;
+        *desc = std::string("resident tcgen05 kernel, ") + (v.f16 ? "FP16" : "FP32") + " accumulator, " +
+                (v.bytes ? "byte" : "half2") + " counters, " + (v.shfl ? "shuffle" : "shared-memory") +
+                " replica exchange";
+    } else if (use_tcs) {
+        *algo = SSQA_ALGO_STREAMED;
+        *desc = std::string("streamed tcgen05 kernel, FP32 accumulator, ") +
+                (I->tc.KB >= 160 ? "two column groups per CTA" : "one column group per CTA");
+    } else {
+        *algo = SSQA_ALGO_DELTA;
+        *desc = "delta-field CUDA-core path (no tensor path takes this problem: " + why +
+                (why_s.empty() || why_s == why ? std::string() : "; " + why_s) + ")";
+    }
+    return SSQA_OK;
+}
+
 struct DevBuf {
     void *p = nullptr;
     cudaStream_t s = nullptr;
@@ -574,28 +645,7 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     const size_t nsp = cols * I->N;
     const int d = p->delay;
 
-    AnnealArgs a{};
-    a.N = I->N;
-    a.R = p->R;
-    a.trials = p->trials;
-    a.cycles = p->cycles;
-    a.I0 = p->I0;
-    a.alpha = p->alpha;
-    a.n_rnd = p->n_rnd;
-    a.jperp_min = p->jperp_min;
-    a.jperp_step = (p->jperp_max - p->jperp_min) / p->beta;
-    a.beta = p->beta;
-    a.tau = p->tau;
-    a.delay = d;
-    a.both = p->coupling == SSQA_COUPLING_BOTH;
-    a.init_mode = p->init_mode;
-    a.start_cycle = p->start_cycle;
-    a.trial_offset = p->trial_offset;
-    a.seed = p->seed;
-    a.i0_max = p->i0_max;
-    a.i0_mult = p->i0_mult;
-    a.i0_tau = p->i0_tau;
-    a.track_best = p->flags & SSQA_FLAG_TRACK_BEST;
+    AnnealArgs a = make_args(I, p);
     a.J = dc->J;
     a.J_pad = dc->J_pad;
     a.Np = dc->Np;
@@ -648,17 +698,10 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
         }
     }
 
-    std::string why, why_s;
-    bool use_tc = false, use_tcs = false;
-    if (p->algo == SSQA_ALGO_STREAMED) {
-        use_tcs = tcs_supported(I->tc, a, &why_s);
-        if (!use_tcs) return fail(SSQA_ERR_UNSUPPORTED, "streamed tensor path: " + why_s);
-    } else if (p->algo == SSQA_ALGO_TENSOR || p->algo == SSQA_ALGO_AUTO) {
-        use_tc = tc_supported(I->tc, a, &why);
-        if (!use_tc) use_tcs = tcs_supported(I->tc, a, &why_s);
-        if (p->algo == SSQA_ALGO_TENSOR && !use_tc && !use_tcs)
-            return fail(SSQA_ERR_UNSUPPORTED, "tensor path: " + why + "; streamed tensor path: " + why_s);
-    }
+    int algo = SSQA_ALGO_AUTO;
+    std::string desc;
+    if ((rc = choose_path(I, p, a, &algo, &desc))) return rc;
+    const bool use_tc = algo == SSQA_ALGO_TENSOR, use_tcs = algo == SSQA_ALGO_STREAMED;
     bool done = false;
     if (use_tc) {
         rc = tc_anneal(I->tc, *dc, a, st);
@@ -670,7 +713,7 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
         // a resumed state the byte counters cannot hold falls back to the CUDA-core paths
         done = !(rc == SSQA_ERR_UNSUPPORTED && p->algo == SSQA_ALGO_AUTO);
     }
-    if (!done && p->algo == SSQA_ALGO_PLAIN) {
+    if (!done && algo == SSQA_ALGO_PLAIN) {
         DevBuf scratch;
         if ((e = alloc(scratch, plain_scratch_bytes(a)))) return cuda_fail(e, "ssqa_anneal: scratch allocation");
         rc = plain_anneal(a, scratch.p, st);
@@ -700,6 +743,32 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     }
     if ((e = cudaGetLastError())) return cuda_fail(e, "ssqa_anneal");
     return SSQA_OK;
+}
+
+extern "C" int ssqa_plan(const ssqa_ising *I, const ssqa_params *p, char *desc, size_t len) {
+    if (!I || !p) return fail(SSQA_ERR_INVALID_ARG, "ssqa_plan: NULL argument");
+    ssqa_result dummy{};
+    int8_t one = 0;
+    int32_t is = 0;
+    int64_t e = 0;
+    int32_t bc = 0;
+    dummy.sigma = &one;
+    dummy.is_state = &is;
+    dummy.sigma_hist = &one;
+    dummy.e_best = &e;
+    dummy.best_cycle = &bc;
+    int rc = validate(I, p, &dummy);
+    if (rc) return rc;
+    const AnnealArgs a = make_args(I, p);
+    int algo = SSQA_ALGO_AUTO;
+    std::string d;
+    if ((rc = choose_path(I, p, a, &algo, &d))) return rc;
+    if (desc && len) {
+        const size_t n = std::min(len - 1, d.size());
+        std::memcpy(desc, d.data(), n);
+        desc[n] = 0;
+    }
+    return algo;
 }
 
 extern "C" int ssqa_energy(const ssqa_ising *I, const int8_t *sigma, int64_t count, int64_t *E_out, uint32_t flags,

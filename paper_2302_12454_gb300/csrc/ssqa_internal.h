@@ -125,6 +125,13 @@ int energy_launch(const int8_t *J_pad, int32_t Np, const int32_t *h, int32_t N, 
 
 // Tensor-core path: whether the resident kernel can run this problem.
 bool tc_supported(const TcImage &img, const AnnealArgs &a, std::string *why);
+// Variant of the resident kernel for a problem it supports: byte or half2
+// counters, shuffle or shared-memory replica exchange, FP16 or FP32
+// accumulator.
+struct TcVariant {
+    bool bytes = false, shfl = false, f16 = false;
+};
+TcVariant tc_variant(const TcImage &img, const AnnealArgs &a);
 int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream);
 
 // I0 of cycle t: fixed, or the SSA schedule of Sec. 4.4.

@@ -1,11 +1,11 @@
 // ssqa_anneal_noalloc: the plain CUDA-core anneal (one launch per cycle) for
 // callers that cannot allocate device memory.
 //
-// Who cannot allocate: code that runs while a CUDA stream is being captured
-// into a graph (allocation calls are not capturable in every capture mode),
-// plugins and real-time loops inside host frameworks that hand out all
+// Who cannot allocate: plugins inside host frameworks that hand out all
 // device memory from their own pools and forbid cudaMalloc after start-up,
-// and deployments that fix their whole device footprint at initialisation.
+// real-time loops in which an allocation (which may synchronise the device)
+// would break the timing, and deployments that fix their whole device
+// footprint at initialisation.
 // Such callers pass every input and output buffer themselves; the scratch
 // this path needs between cycle launches (the spin history ring and two
 // per-column energy accumulators) lives in one file-scope device array that
@@ -91,12 +91,27 @@ int check_params(int32_t N, const ssqa_params *p, const ssqa_result *r) {
     return SSQA_OK;
 }
 
+// The kernels read J rows as 16-byte vectors, h and the counters as int32,
+// and write the energies as int64: a caller's pointer that is not aligned to
+// its access width (an offset view of a larger buffer, say) is rejected here,
+// before anything is launched, instead of faulting on the device.
+int check_alignment(const int8_t *J_padded, const int32_t *h, const ssqa_result *r) {
+    auto bad = [](const void *q, uintptr_t a) { return q != nullptr && (reinterpret_cast<uintptr_t>(q) % a) != 0; };
+    if (bad(J_padded, 16)) return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: J_padded must be 16-byte aligned");
+    if (bad(h, 4) || bad(r->is_state, 4) || bad(r->best_cycle, 4))
+        return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: h, is_state and best_cycle must be 4-byte aligned");
+    if (bad(r->e_final, 8) || bad(r->e_best, 8) || bad(r->e_trace, 8))
+        return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: e_final, e_best and e_trace must be 8-byte aligned");
+    return SSQA_OK;
+}
+
 }  // namespace
 
 extern "C" int ssqa_anneal_noalloc(int32_t N, const int8_t *J_padded, const int32_t *h, const ssqa_params *params,
                                    ssqa_result *out, void *cuda_stream) {
     if (!J_padded || !h || !params || !out) return ssqa::fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_noalloc: NULL argument");
     if (int rc = check_params(N, params, out)) return rc;
+    if (int rc = check_alignment(J_padded, h, out)) return rc;
     const ssqa_params &p = *params;
     ssqa::AnnealArgs a{};
     a.N = N;

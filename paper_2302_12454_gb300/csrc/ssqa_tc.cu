@@ -126,6 +126,19 @@ bool tc_supported(const TcImage &img, const AnnealArgs &a, std::string *why) {
     return plan(img, a, &L, why);
 }
 
+TcVariant tc_variant(const TcImage &img, const AnnealArgs &a) {
+    // byte counters: counters fit a biased byte, alpha = 1, and a fresh start
+    // (resumed counters may lie outside the byte range); shuffle exchange
+    // when R divides 32; FP16 accumulator when every partial sum is an
+    // integer of magnitude <= 2048, and so is D + h / jm (the energy's term)
+    TcVariant v;
+    const int32_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
+    v.bytes = i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
+    v.shfl = v.bytes && 32 % a.R == 0;
+    v.f16 = v.bytes && img.max_row_sum + img.max_h_unit <= 2048;
+    return v;
+}
+
 int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream) {
     Layout L;
     std::string why;
@@ -147,14 +160,8 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.G = L.G;
     p.crow[0] = img.chunk_rows[0];
     p.crow[1] = img.chunk_rows[1];
-    // byte counters: counters fit a biased byte, alpha = 1, and a fresh start
-    // (resumed counters may lie outside the byte range); shuffle exchange
-    // when R divides 32; FP16 accumulator when every partial sum is an
-    // integer of magnitude <= 2048, and so is D + h / jm (the energy's term)
-    const int32_t i0_top = a.i0_max > a.I0 ? a.i0_max : a.I0;
-    const bool fast = i0_top <= 127 && a.alpha == 1 && a.init_mode != SSQA_INIT_FROM_STATE;
-    const bool shfl = fast && 32 % a.R == 0;
-    const bool f16 = fast && img.max_row_sum + img.max_h_unit <= 2048;
+    const TcVariant var = tc_variant(img, a);
+    const bool fast = var.bytes, shfl = var.shfl, f16 = var.f16;
     for (int ch = 0; ch < 2; ++ch) {
         // instruction descriptor, kind::f8f6f4: D f16 (bits 4-5 = 0) or f32 (1),
         // A and B E4M3 (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.

@@ -664,7 +664,8 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                     const long long s = static_cast<long long>(eacc[c]);
                     eacc[c] = 0ull;
                     const int64_t E = -(int64_t(p.jm) * s) / 2;
-                    if (kTrack && E < e_best) {
+                    // E_best covers sigma(t0 + 1 .. t0 + cycles): not the start state
+                    if (kTrack && it > 0 && E < e_best) {
                         e_best = E;
                         best_cycle = int32_t(t);
                     }

@@ -175,3 +175,27 @@ def test_anneal_out_buffers_are_checked():
                 {"E_final": np.zeros((3, 2), np.int64)}, {"sigma": np.zeros((2, 16, 3), np.int8).transpose(0, 2, 1)}):
         with pytest.raises(ValueError):
             S.anneal(I, R=3, cycles=1, trials=2, seed=1, out=bad)
+
+
+def test_noalloc_rejects_misaligned_pointers_before_any_launch():
+    """ssqa_anneal_noalloc checks the alignment of every caller pointer on
+    the host.  The pointers here are fake device addresses that are never
+    dereferenced: each call must return SSQA_ERR_INVALID_ARG before touching
+    the device.  (Skipped where a GPU is present, so that a checking bug can
+    never turn into a launch on fake addresses.)"""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("host-only check; runs where no GPU is present")
+    L = S.lib()
+    p = S.make_params(R=4, cycles=3, trials=2, seed=1)
+    p.flags = S.FLAG_DEVICE_PTRS | S.FLAG_TRACK_BEST
+    base = dict(J=0x10000, h=0x20000, sigma=0x30000, hist=0x40000, Is=0x50000, E=0x60000, Eb=0x70000,
+                bc=0x80000, tr=0x90000)
+    for key, off in (("J", 8), ("J", 1), ("h", 2), ("Is", 1), ("bc", 2), ("E", 4), ("Eb", 2), ("tr", 4)):
+        ptr = dict(base)
+        ptr[key] += off
+        r = S.Result(ptr["sigma"], ptr["hist"], ptr["Is"], ptr["E"], ptr["Eb"], ptr["bc"], ptr["tr"])
+        rc = L.ssqa_anneal_noalloc(36, ctypes.c_void_p(ptr["J"]), ctypes.c_void_p(ptr["h"]), ctypes.byref(p),
+                                   ctypes.byref(r), None)
+        assert rc == S.ERR_INVALID_ARG, (key, off, rc)
+        assert "aligned" in S.last_error(), S.last_error()

@@ -1,9 +1,10 @@
 """The allocation-free anneal (ssqa_anneal_noalloc) against ssqa_anneal.
 
 ssqa_anneal_noalloc serves callers that cannot allocate device memory (for
-instance code running under CUDA stream capture, or plugins whose host
-framework owns every device allocation): it takes only caller-provided
-device buffers and keeps its scratch in a fixed array inside the library.
+instance plugins whose host framework owns every device allocation, or
+real-time loops in which an allocation would synchronise the device): it
+takes only caller-provided device buffers and keeps its scratch in a fixed
+array inside the library.
 This test calls it through the C ABI twice in a row (the shared scratch
 keeps the previous call's contents) and checks both results element by
 element against ssqa_anneal on the same inputs; the method is integer
