@@ -16,6 +16,7 @@ import json
 import math
 import multiprocessing as mp
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -49,18 +50,59 @@ def _oracle_trial(args):
     return time.perf_counter() - t0
 
 
-def oracle_rate(h, J, cfg, cycles, ntrials, cores):
+def _oracle_warm(_):
+    from oracle import oracle as O
+
+    O.lib()
+    return os.getpid()
+
+
+def host_info():
+    """Core count and CPU model of this host (for the CPU-side lines)."""
+    model = platform.processor() or ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k, _, v = ln.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                    model = v.strip() if k.strip() != "CPU part" else f"{platform.machine()} CPU part {v.strip()}"
+                    break
+    except OSError:
+        pass
+    return {"cpu_count": os.cpu_count(), "cpu_model": model or platform.machine(), "machine": platform.machine()}
+
+
+class OraclePool:
+    """Single-threaded oracle processes, one per core, started (spawn) and
+    warmed once, so that timed maps measure the oracle and not process start-up."""
+
+    def __init__(self, cores):
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores) if cores > 1 else None
+        if self.pool is not None:
+            self.pool.map(_oracle_warm, range(cores))
+        else:
+            _oracle_warm(0)
+
+    def map(self, jobs):
+        if self.pool is not None:
+            return self.pool.map(_oracle_trial, jobs, chunksize=1)
+        return [_oracle_trial(j) for j in jobs]
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+
+def oracle_rate(pool, h, J, cfg, cycles, ntrials):
     """Spin-updates/s of the oracle: `ntrials` single-trial anneals of
-    `cycles` cycles, spread over `cores` spawned worker processes."""
+    `cycles` cycles spread over the pool's worker processes."""
     kw = dict(R=cfg["R"], cycles=cycles, trials=1, seed=cfg["seed"], tau=cfg["tau"])
     jobs = [(h, J, kw, tr) for tr in range(ntrials)]
     t0 = time.perf_counter()
-    if cores > 1:
-        with mp.get_context("spawn").Pool(cores) as pool:
-            pool.map(_oracle_trial, jobs)
-    else:
-        for j in jobs:
-            _oracle_trial(j)
+    pool.map(jobs)
     wall = time.perf_counter() - t0
     return h.shape[0] * cfg["R"] * cycles * ntrials / wall, wall
 
@@ -116,7 +158,7 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- our arm
-def large_workloads(S, W, torch, stream, cores=0):
+def large_workloads(S, W, torch, stream, pool=None):
     """The two large configurations (one anneal each, default path = the
     streamed tensor kernel), timed with CUDA events after a warm-up call that
     uploads the instance.  Informational: the headline is the batched N = 400
@@ -152,11 +194,11 @@ def large_workloads(S, W, torch, stream, cores=0):
              "tflops": 2.0 * N * N * R * T * C / t / 1e12}
         if cfg["kind"] == "gi":
             r["p_s"] = float((E.min(dim=1).values.cpu().numpy() == -off).mean())
-        if cores:
+        if pool is not None:
             oc = 2 if cfg["kind"] == "gi" else 1
-            rate, wall = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, oc, cores, cores)
-            r["oracle"] = {"value": rate, "unit": "spin-updates/s", "cores": cores,
-                           "sample": f"{cores} trials x {oc} cycles ({wall:.1f} s)", "ratio": r["value"] / rate}
+            rate, wall = oracle_rate(pool, h.astype(np.int64), J.astype(np.int64), cfg, oc, pool.cores)
+            r["oracle"] = {"value": rate, "unit": "spin-updates/s", "cores": pool.cores,
+                           "sample": f"{pool.cores} trials x {oc} cycles ({wall:.1f} s)", "ratio": r["value"] / rate}
         res[name] = r
         del I
     return res
@@ -388,16 +430,19 @@ def run_ours(args, rank, world):
         out["served"] = SB.run(S, W, count=64, n_min=8, n_max=20, cycles_set=(500, 1000, 2000), slots=32,
                                plain_sample=8)
         out["rows"] = row_timings(S, torch, stream, I, cfg, sigma, Is, E, ms_per_step)
+        pool = None if args.no_cpu_baseline else OraclePool(min(64, os.cpu_count() or 1))
         if not args.no_large:
-            out["large_workloads"] = large_workloads(S, W, torch, stream,
-                                                     0 if args.no_cpu_baseline else min(16, os.cpu_count() or 1))
-        if not args.no_cpu_baseline:
-            cores = min(16, os.cpu_count() or 1)
-            rate, cwall = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, cycles, 2 * cores, cores)
-            rate1, wall1 = oracle_rate(h.astype(np.int64), J.astype(np.int64), cfg, 500, 1, 1)
+            out["large_workloads"] = large_workloads(S, W, torch, stream, pool)
+        if pool is not None:
+            cores = pool.cores
+            rate, cwall = oracle_rate(pool, h.astype(np.int64), J.astype(np.int64), cfg, cycles, 2 * cores)
+            pool1 = OraclePool(1)
+            rate1, wall1 = oracle_rate(pool1, h.astype(np.int64), J.astype(np.int64), cfg, 500, 1)
+            pool.close()
             out["cpu_baseline"] = {"value": rate, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
                                    "sample": f"{2 * cores} trials x {cycles} cycles of the same workload, one "
                                              f"single-threaded oracle process per core ({cwall:.1f} s)",
+                                   "host": host_info(),
                                    "single_core": {"value": rate1, "sample": f"1 trial x 500 cycles ({wall1:.1f} s)"}}
         print(json.dumps(out), flush=True)
     if dist:
@@ -415,15 +460,17 @@ def run_reference(args, rank, world):
     a = O.gen_er_graph(cfg["n"], W.p_q32(cfg["p"]), cfg["graph_seed"])
     b, _ = O.permute_graph(a, cfg["perm_seed"])
     h, J, off = O.build_gi_ising(a, b)
-    cores = min(16, os.cpu_count() or 1)
+    cores = min(64, os.cpu_count() or 1)
     cycles = 100
+    pool = OraclePool(cores)  # started and warmed outside the timed steps
     for _ in range(args.warmup):
-        oracle_rate(h, J, cfg, 20, cores, cores)
+        oracle_rate(pool, h, J, cfg, 20, cores)
     rates, walls = [], []
     for _ in range(args.steps):
-        r, w = oracle_rate(h, J, cfg, cycles, cores, cores)
+        r, w = oracle_rate(pool, h, J, cfg, cycles, cores)
         rates.append(r)
         walls.append(w)
+    pool.close()
     value = float(cycles * cores * h.shape[0] * cfg["R"] * len(walls) / sum(walls))
     sample = f"{cores} trials x {cycles} cycles per step (one single-threaded oracle process per core)"
     out = {"impl": "reference", "metric": "spin-updates/sec", "value": value, "unit": "spin-updates/s",
@@ -432,7 +479,7 @@ def run_reference(args, rank, world):
            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
            "config": {"workload": f"{WORKLOAD} (bounded sample: {sample})"},
            "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "host": host_info()},
            "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -8,10 +8,12 @@
 // A thread-block cluster of CS CTAs covers all chunks of its column group(s);
 // chunk ch belongs to cluster rank ch mod CS.  Per cycle:
 //   producer warp  streams, for each owned chunk, the K-blocks of A (sigma(t)
-//                  of 128 columns, 4 KB per group) and B (J rows of the chunk,
-//                  8 KB) from L2 into a 12-stage shared-memory ring (bulk
-//                  async copies completing on mbarriers);
-//   MMA warp       issues per stage one tcgen05.mma kind::f8f6f4 (M 128,
+//                  of 128 columns, 4 KB per group and K-block) and B (J rows
+//                  of the chunk, 8 KB per K-block) from L2 into a shared-memory
+//                  ring whose stages hold kKps consecutive K-blocks, one bulk
+//                  async copy per operand and stage (consecutive K-blocks are
+//                  contiguous in both images), completing on mbarriers;
+//   MMA warp       issues per K-block one tcgen05.mma kind::f8f6f4 (M 128,
 //                  N <= 256, K 32) per group, all groups on the same B block;
 //   8 epilogue warps turn finished accumulators into sigma(t+1) of the chunk
 //                  (Eq. 6a-6c, the same packed-half2 arithmetic as the resident
@@ -43,11 +45,16 @@ namespace ssqa {
 namespace tcs {
 using namespace tc;
 
-constexpr int kStages = 12;
+// A bulk copy's delivery rate into an SM follows the bytes it keeps in
+// flight: with about 192 KB outstanding an SM receives ~75 B/clk, with 12 KB
+// stages of one K-block it received ~23.  So a stage carries kKps K-blocks
+// (48 KB single, 64 KB dual) and the ring holds 4 (single) or 3 (dual) of them.
+constexpr int kKps = 4;             // K-blocks per ring stage
 constexpr int kABytes = 128 * 32;   // one K-block of A
 constexpr int kBBytes = 256 * 32;   // one K-block of a B chunk
-constexpr int kStageBytes = 2 * kABytes + kBBytes;  // dual mode: A of both column groups, one B block
-constexpr int kStageBytes1 = kABytes + kBBytes;     // single mode
+constexpr int kStageBytes = kKps * (2 * kABytes + kBBytes);  // dual mode: A of both column groups, one B run
+constexpr int kStageBytes1 = kKps * (kABytes + kBBytes);     // single mode
+constexpr int kStagesDual = 3, kStagesSingle = 4;
 constexpr int kEpi = 8;             // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kThr = (2 + kEpi) * 32;
 
@@ -103,9 +110,12 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *ring = sm;
-    // stage = A (one block per group) then the B block
+    // stage = A run of group 0 [kKps][128 x 32], (dual) A run of group 1, then
+    // the B run [kKps][256 x 32]
+    constexpr int kStages = kDual ? kStagesDual : kStagesSingle;
     constexpr int sbytes = kDual ? kStageBytes : kStageBytes1;
-    constexpr int boff = kDual ? 2 * kABytes : kABytes;
+    constexpr int a2off = kKps * kABytes;
+    constexpr int boff = (kDual ? 2 : 1) * kKps * kABytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + kStages * sbytes);
     uint64_t *empty = full + kStages;
     uint64_t *tfull = empty + kStages;   // [2]
@@ -204,20 +214,21 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     const int ch = rank + m * p.CS;
                     const uint8_t *Bc = p.B + int64_t(ch) * p.KB * kBBytes;
                     if (m > 0 && *reinterpret_cast<volatile int *>(p.err)) abort_run = true;
-                    for (int kb = 0; kb < p.KB && !abort_run; ++kb) {
+                    for (int kb = 0; kb < p.KB && !abort_run; kb += kKps) {
+                        const int nkb = p.KB - kb < kKps ? p.KB - kb : kKps;
                         if (!mbar_wait(&empty[ps], uint32_t(pph))) {
                             atomicExch(p.err, 1);
                             abort_run = true;
                             break;
                         }
-                        // A of each group, then the B block both groups' MMAs share
+                        // nkb K-blocks: A of each group, then the B run both groups' MMAs share
                         uint8_t *st = ring + ps * sbytes;
-                        mbar_expect_tx(&full[ps], uint32_t(ng * kABytes + kBBytes));
-                        bulk_g2s(st, Ag0 + cur_off + int64_t(kb) * kABytes, kABytes, &full[ps]);
+                        mbar_expect_tx(&full[ps], uint32_t(nkb * (ng * kABytes + kBBytes)));
+                        bulk_g2s(st, Ag0 + cur_off + int64_t(kb) * kABytes, uint32_t(nkb * kABytes), &full[ps]);
                         if (kDual && ng > 1)
-                            bulk_g2s(st + kABytes, Ag0 + slot_stride + cur_off + int64_t(kb) * kABytes, kABytes,
-                                     &full[ps]);
-                        bulk_g2s(st + boff, Bc + int64_t(kb) * kBBytes, kBBytes, &full[ps]);
+                            bulk_g2s(st + a2off, Ag0 + slot_stride + cur_off + int64_t(kb) * kABytes,
+                                     uint32_t(nkb * kABytes), &full[ps]);
+                        bulk_g2s(st + boff, Bc + int64_t(kb) * kBBytes, uint32_t(nkb * kBBytes), &full[ps]);
                         ++nis;
                         if (++ps == kStages) {
                             ps = 0;
@@ -244,7 +255,8 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     }
                     mt_ph ^= 1u << b;
                     tc_fence_after();
-                    for (int kb = 0; kb < p.KB; ++kb) {
+                    for (int kb = 0; kb < p.KB; kb += kKps) {
+                        const int nkb = p.KB - kb < kKps ? p.KB - kb : kKps;
                         if (!mbar_wait(&full[ms], uint32_t(mph))) {
                             atomicExch(p.err, 1);
                             abort_run = true;
@@ -252,10 +264,15 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                         }
                         tc_fence_after();
                         const uint32_t st = smem_u32(ring + ms * sbytes);
-                        const uint64_t bd = smem_desc(st + uint32_t(boff), 128u, 256u);
-                        mma_f8f6f4(tmem + uint32_t(b * 256), smem_desc(st, 128u, 256u), bd, idesc, kb > 0 ? 1u : 0u);
-                        if (kDual && ng > 1)
-                            mma_f8f6f4(tmem + 256u, smem_desc(st + kABytes, 128u, 256u), bd, idesc, kb > 0 ? 1u : 0u);
+                        for (int j = 0; j < nkb; ++j) {
+                            const uint32_t acc = kb + j > 0 ? 1u : 0u;
+                            const uint64_t bd = smem_desc(st + uint32_t(boff + j * kBBytes), 128u, 256u);
+                            mma_f8f6f4(tmem + uint32_t(b * 256), smem_desc(st + uint32_t(j * kABytes), 128u, 256u), bd,
+                                       idesc, acc);
+                            if (kDual && ng > 1)
+                                mma_f8f6f4(tmem + 256u, smem_desc(st + uint32_t(a2off + j * kABytes), 128u, 256u), bd,
+                                           idesc, acc);
+                        }
                         mma_commit(&empty[ms]);  // frees the stage when these MMAs complete
                         if (++ms == kStages) {
                             ms = 0;
@@ -699,7 +716,8 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
     }
     void (*fn)(SParams) = a.track_best ? (p.dual ? ssqa_tcs_kernel<true, true> : ssqa_tcs_kernel<true, false>)
                                        : (p.dual ? ssqa_tcs_kernel<false, true> : ssqa_tcs_kernel<false, false>);
-    const int smem = kStages * (p.dual ? kStageBytes : kStageBytes1) + 1024 + 512;  // ring + alignment + barriers
+    const int smem = p.dual ? kStagesDual * kStageBytes + 1024 + 512   // ring + alignment + barriers
+                            : kStagesSingle * kStageBytes1 + 1024 + 512;
     configure_once(fn, smem);
     cudaLaunchConfig_t cfg{};
     cfg.blockDim = dim3(kThr, 1, 1);
