@@ -62,7 +62,7 @@ struct SParams {
     AnnealArgs a;
     const uint8_t *B;       // [NCH][KB][256 x 32] blocks
     uint8_t *A;             // [groups][L][KB][128 x 32] blocks
-    uint8_t *IsB;           // [cols][Np] counters + 128
+    uint8_t *IsB;           // [Np / 16][cols][16] counters + 128 (a warp's 16-byte loads are contiguous)
     const float *hf;        // h / jm as float (N)
     unsigned long long *eacc;  // [2][cols]
     int64_t *ebest, *efin;     // [cols]
@@ -328,6 +328,29 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     nq2 = odd ? ph1.x[2] : ph1.x[0];
                     nq3 = odd ? ph1.x[3] : ph1.x[1];
                 }
+                // Granule g of the chunk (q = g / 2, hh = g % 2): spins i0 .. i0 + 15 of
+                // word wbase + 4 (q % 2) + q / 2.  Its counters and its upper ring
+                // neighbour's sigma(t - d) do not depend on this cycle's MMAs; in single
+                // mode all eight granules' values are loaded before the accumulator is
+                // awaited, so that their L2 latencies overlap the wait and each other.
+                auto gran_i0 = [&](int g) { return 32 * (wbase + 4 * ((g >> 1) & 1) + (g >> 2)) + 16 * (g & 1); };
+                auto is_ptr = [&](int i0) { return p.IsB + (int64_t(i0 >> 4) * cols + gcol) * 16; };
+                auto nu_ptr = [&](int i0) { return Aold + int64_t(i0 >> 5) * kABytes + blk_off(nb_up, i0 & 31); };
+                auto gran_loads = [&](int g, uint4 &isv, uint4 &nu) {
+                    const int i0 = gran_i0(g);
+                    if (update && valid && i0 < p.N16) {
+                        isv = *reinterpret_cast<const uint4 *>(is_ptr(i0));
+                        nu = *reinterpret_cast<const uint4 *>(nu_ptr(i0));
+                    } else {
+                        isv = make_uint4(0, 0, 0, 0);
+                        nu = isv;
+                    }
+                };
+                uint4 pis[kDual ? 1 : 8], pnu[kDual ? 1 : 8];
+                if constexpr (!kDual) {
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) gran_loads(g, pis[g], pnu[g]);
+                }
                 if (gi == 0) {  // the chunk's accumulators (of both groups)
                     const bool ok = mbar_wait(&tfull[b], (et_ph >> b) & 1u);
                     if (__any_sync(0xffffffffu, !ok)) {
@@ -338,83 +361,87 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     et_ph ^= 1u << b;
                     tc_fence_after();
                 }
-#pragma unroll 1
-                for (int q = 0; q < 4; ++q) {
-                    const int w = wbase + 4 * (q & 1) + (q >> 1);
+                auto granule = [&](int g, const uint4 isv, const uint4 nu) {
+                    const int q = g >> 1, hh = g & 1;
+                    const int i0 = gran_i0(g);
+                    if (i0 >= p.N16) return;  // warp-uniform
                     const uint32_t nw = q == 0 ? nq0 : (q == 1 ? nq1 : (q == 2 ? nq2 : nq3));
+                    uint32_t f[16];
+                    __syncwarp();
+                    tmem_ld16_issue(tmem + (uint32_t(qd * 32) << 16) + uint32_t((b + gi) * 256 + (i0 - 256 * ch)), f);
+                    tmem_ld_wait(f);
+                    if (!valid) return;
+                    const int kb = i0 >> 5;
+                    const uint32_t ob = blk_off(c, i0 & 31);
+                    if (energy) {
+                        // sigma_i (D_i + h_i / jm) = sigma_i (sum_j J_ij sigma_j + 2 h_i) / jm; a
+                        // 16-spin partial sum is an exact float (|terms| <= 2^15)
+                        const uint4 so = *reinterpret_cast<const uint4 *>(Acur + int64_t(kb) * kABytes + ob);
+                        const uint32_t sw[4] = {so.x, so.y, so.z, so.w};
+                        float tsum = 0.f;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int i = i0 + e;
+                            if (i >= a.N) break;
+                            const float y = __uint_as_float(f[e]) + __ldg(&p.hf[i]);
+                            const uint32_t sgn = (sw[e >> 2] << (24 - 8 * (e & 3))) & 0x80000000u;
+                            tsum += __uint_as_float(__float_as_uint(y) ^ sgn);
+                        }
+                        esum += static_cast<long long>(tsum);
+                        if (!update) return;
+                    }
+                    // ring neighbours' sigma(t - d) (FP8 bytes, sign bit 7)
+                    const uint32_t nuw[4] = {nu.x, nu.y, nu.z, nu.w};
+                    uint32_t ndw[4] = {0, 0, 0, 0};
+                    if (a.both) {
+                        const uint4 nd = *reinterpret_cast<const uint4 *>(Aold + int64_t(kb) * kABytes +
+                                                                          blk_off(nb_dn, i0 & 31));
+                        ndw[0] = nd.x;
+                        ndw[1] = nd.y;
+                        ndw[2] = nd.z;
+                        ndw[3] = nd.w;
+                    }
+                    const uint32_t isw[4] = {isv.x, isv.y, isv.z, isv.w};
+                    uint32_t isn[8];
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq) {
+                        const int j = hh * 8 + qq;
+                        const uint32_t x2 = pack_h2(f[2 * qq], f[2 * qq + 1]);
+                        const uint32_t n2 = ((nw << j) & kSignPair) ^ p.NR2;
+                        // bytes 2qq, 2qq+1 of the neighbour row: signs to bits 15 / 31
+                        const uint32_t sel = (qq & 1) ? 0x3727 : 0x1707;
+                        const uint32_t c2 = (__byte_perm(nuw[qq >> 1], 0, sel) & kSignPair) ^ JP2;
+                        __half2 y = __hfma2(u2h(x2), u2h(p.JM2), u2h(n2));
+                        y = __hadd2(y, u2h(c2));
+                        if (a.both)
+                            y = __hadd2(y, u2h((__byte_perm(ndw[qq >> 1], 0, sel) & kSignPair) ^ JP2));
+                        const uint32_t ib = __byte_perm(isw[qq >> 1], 0x64646464u, (qq & 1) ? 0x4342 : 0x4140);
+                        const __half2 v = __hadd2(u2h(ib), y);
+                        const __half2 mm = __hmax2(v, u2h(LO2));
+                        const uint32_t ge = __hge2_mask(v, u2h(TOP2));
+                        isn[qq] = (ge & HI2) | (~ge & h2u(mm));
+                    }
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int mq = 0; mq < 4; ++mq) pk[mq] = __byte_perm(isn[2 * mq], isn[2 * mq + 1], 0x6420);
+                    *reinterpret_cast<uint4 *>(is_ptr(i0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    uint4 bo;
+                    bo.x = (~pk[0] & 0x80808080u) | 0x38383838u;
+                    bo.y = (~pk[1] & 0x80808080u) | 0x38383838u;
+                    bo.z = (~pk[2] & 0x80808080u) | 0x38383838u;
+                    bo.w = (~pk[3] & 0x80808080u) | 0x38383838u;
+                    if (i0 + 16 > a.N) bo = mask_tail(bo, i0, a.N);
+                    *reinterpret_cast<uint4 *>(Anext + int64_t(kb) * kABytes + ob) = bo;
+                };
+                if constexpr (!kDual) {
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) granule(g, pis[g], pnu[g]);
+                } else {
 #pragma unroll 1
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int i0 = 32 * w + 16 * hh;
-                        if (i0 >= p.N16) continue;  // warp-uniform
-                        uint32_t f[16];
-                        __syncwarp();
-                        tmem_ld16_issue(tmem + (uint32_t(qd * 32) << 16) + uint32_t((b + gi) * 256 + (i0 - 256 * ch)), f);
-                        tmem_ld_wait(f);
-                        if (!valid) continue;
-                        const int kb = i0 >> 5;
-                        const uint32_t ob = blk_off(c, i0 & 31);
-                        if (energy) {
-                            // sigma_i (D_i + h_i / jm) = sigma_i (sum_j J_ij sigma_j + 2 h_i) / jm; a
-                            // 16-spin partial sum is an exact float (|terms| <= 2^15)
-                            const uint4 so = *reinterpret_cast<const uint4 *>(Acur + int64_t(kb) * kABytes + ob);
-                            const uint32_t sw[4] = {so.x, so.y, so.z, so.w};
-                            float tsum = 0.f;
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const int i = i0 + e;
-                                if (i >= a.N) break;
-                                const float y = __uint_as_float(f[e]) + __ldg(&p.hf[i]);
-                                const uint32_t sgn = (sw[e >> 2] << (24 - 8 * (e & 3))) & 0x80000000u;
-                                tsum += __uint_as_float(__float_as_uint(y) ^ sgn);
-                            }
-                            esum += static_cast<long long>(tsum);
-                            if (!update) continue;
-                        }
-                        // ring neighbours' sigma(t - d) (FP8 bytes, sign bit 7)
-                        const uint4 nu = *reinterpret_cast<const uint4 *>(Aold + int64_t(kb) * kABytes +
-                                                                          blk_off(nb_up, i0 & 31));
-                        const uint32_t nuw[4] = {nu.x, nu.y, nu.z, nu.w};
-                        uint32_t ndw[4] = {0, 0, 0, 0};
-                        if (a.both) {
-                            const uint4 nd = *reinterpret_cast<const uint4 *>(Aold + int64_t(kb) * kABytes +
-                                                                              blk_off(nb_dn, i0 & 31));
-                            ndw[0] = nd.x;
-                            ndw[1] = nd.y;
-                            ndw[2] = nd.z;
-                            ndw[3] = nd.w;
-                        }
-                        const uint4 isv = *reinterpret_cast<const uint4 *>(p.IsB + gcol * a.Np + i0);
-                        const uint32_t isw[4] = {isv.x, isv.y, isv.z, isv.w};
-                        uint32_t isn[8];
-#pragma unroll
-                        for (int qq = 0; qq < 8; ++qq) {
-                            const int j = hh * 8 + qq;
-                            const uint32_t x2 = pack_h2(f[2 * qq], f[2 * qq + 1]);
-                            const uint32_t n2 = ((nw << j) & kSignPair) ^ p.NR2;
-                            // bytes 2qq, 2qq+1 of the neighbour row: signs to bits 15 / 31
-                            const uint32_t sel = (qq & 1) ? 0x3727 : 0x1707;
-                            const uint32_t c2 = (__byte_perm(nuw[qq >> 1], 0, sel) & kSignPair) ^ JP2;
-                            __half2 y = __hfma2(u2h(x2), u2h(p.JM2), u2h(n2));
-                            y = __hadd2(y, u2h(c2));
-                            if (a.both)
-                                y = __hadd2(y, u2h((__byte_perm(ndw[qq >> 1], 0, sel) & kSignPair) ^ JP2));
-                            const uint32_t ib = __byte_perm(isw[qq >> 1], 0x64646464u, (qq & 1) ? 0x4342 : 0x4140);
-                            const __half2 v = __hadd2(u2h(ib), y);
-                            const __half2 mm = __hmax2(v, u2h(LO2));
-                            const uint32_t ge = __hge2_mask(v, u2h(TOP2));
-                            isn[qq] = (ge & HI2) | (~ge & h2u(mm));
-                        }
-                        uint32_t pk[4];
-#pragma unroll
-                        for (int mq = 0; mq < 4; ++mq) pk[mq] = __byte_perm(isn[2 * mq], isn[2 * mq + 1], 0x6420);
-                        *reinterpret_cast<uint4 *>(p.IsB + gcol * a.Np + i0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        uint4 bo;
-                        bo.x = (~pk[0] & 0x80808080u) | 0x38383838u;
-                        bo.y = (~pk[1] & 0x80808080u) | 0x38383838u;
-                        bo.z = (~pk[2] & 0x80808080u) | 0x38383838u;
-                        bo.w = (~pk[3] & 0x80808080u) | 0x38383838u;
-                        if (i0 + 16 > a.N) bo = mask_tail(bo, i0, a.N);
-                        *reinterpret_cast<uint4 *>(Anext + int64_t(kb) * kABytes + ob) = bo;
+                    for (int g = 0; g < 8; ++g) {
+                        uint4 isv, nu;
+                        gran_loads(g, isv, nu);
+                        granule(g, isv, nu);
                     }
                 }
                 if (gi)
@@ -548,8 +575,9 @@ __global__ void tcs_init_kernel(SParams p, const uint8_t *a_w, int nh) {
     const int64_t cols = int64_t(a.trials) * a.R;
     for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < cols * a.Np;
          x += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t col = x / a.Np;
-        const int i = int(x % a.Np);
+        // x = ((i / 16) * cols + col) * 16 + i % 16
+        const int64_t col = (x / 16) % cols;
+        const int i = int((x / (16 * cols)) * 16 + x % 16);
         int v = 0;
         if (i < a.N && a.init_mode == SSQA_INIT_FROM_STATE) v = a.Is[col * a.N + i];
         if (v < -128 || v > 127) {
@@ -580,7 +608,7 @@ __global__ void tcs_finish_kernel(SParams p, int64_t tf) {
             for (int l = 0; l < a.delay; ++l)
                 a.hist[((trial * a.delay + l) * a.R + kr) * int64_t(a.N) + i] =
                     (Ag[slot_of(tf - 1 - l, p.L) * p.KB * kABytes + o] & 0x80) ? int8_t(-1) : int8_t(1);
-        a.Is[x] = int32_t(p.IsB[col * a.Np + i]) - 128;
+        a.Is[x] = int32_t(p.IsB[(int64_t(i >> 4) * cols + col) * 16 + (i & 15)]) - 128;
     }
 }
 
