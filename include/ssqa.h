@@ -287,6 +287,17 @@ int ssqa_energy(const ssqa_ising *ising, const int8_t *sigma, int64_t count, int
  * p_target outside (0, 1). */
 double ssqa_tts(double t, double p_s, double p_target);
 
+/* Bound of the device-side waits of the tensor-core kernels, in SM clocks.
+ * Every wait of a kernel for its tensor cores, its copies or another warp or
+ * CTA gives up after this many clocks: the kernel then stops its work, lets
+ * its own operations in flight finish (with a fixed bound of 4e9 clocks),
+ * frees its tensor memory and returns, and the call reports
+ * SSQA_ERR_TIMEOUT; the CUDA context stays usable.  0 restores the default
+ * of 8e9 clocks (about 4 s at 2 GHz).  Process-wide; applies to launches made
+ * after the call.  Not in the paper: it bounds a failure (a stalled device)
+ * instead of hanging.  Errors: SSQA_ERR_INVALID_ARG (clocks < 0). */
+int ssqa_set_wait_limit(int64_t clocks);
+
 /* Human-readable description of the last error on this thread ("" if none). */
 const char *ssqa_last_error(void);
 

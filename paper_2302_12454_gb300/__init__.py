@@ -73,6 +73,7 @@ def lib():
         L.ssqa_energy.argtypes = [vp, vp, i64, vp, u32, vp]
         L.ssqa_plan.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_char_p, ctypes.c_size_t]
         L.ssqa_anneal_noalloc.argtypes = [i32, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
+        L.ssqa_set_wait_limit.argtypes = [i64]
         L.ssqa_tts.argtypes = [ctypes.c_double] * 3
         L.ssqa_tts.restype = ctypes.c_double
         L.ssqa_last_error.argtypes = []
@@ -272,6 +273,11 @@ def energy(ising: Ising, sigma) -> np.ndarray:
     E = np.zeros(flat.shape[0], np.int64)
     _check(lib().ssqa_energy(ising.handle, _ptr(flat), flat.shape[0], _ptr(E), 0, None), "energy")
     return E.reshape(s.shape[:-1])
+
+
+def set_wait_limit(clocks: int) -> None:
+    """Bound of the tensor-core kernels' device waits in SM clocks (0: default)."""
+    _check(lib().ssqa_set_wait_limit(int(clocks)), "set_wait_limit")
 
 
 def tts(t: float, p_s: float, p_target: float = 0.99) -> float:

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -18,6 +19,12 @@
 namespace ssqa {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_wait_clocks{0};
+
+long long wait_limit_clocks() {
+    const long long v = g_wait_clocks.load(std::memory_order_relaxed);
+    return v > 0 ? v : 8000000000LL;
+}
 
 int fail(int code, const std::string &msg) {
     g_last_error = msg;
@@ -324,6 +331,12 @@ using namespace ssqa;
 extern "C" {
 
 const char *ssqa_last_error(void) { return g_last_error.c_str(); }
+
+int ssqa_set_wait_limit(int64_t clocks) {
+    if (clocks < 0) return fail(SSQA_ERR_INVALID_ARG, "ssqa_set_wait_limit: clocks must be >= 0");
+    g_wait_clocks.store(clocks, std::memory_order_relaxed);
+    return SSQA_OK;
+}
 
 int ssqa_gen_er_graph(int32_t n, uint32_t p_q32, uint64_t seed, uint8_t *adj) {
     if (n < 1 || n > 65535 || !adj) return fail(SSQA_ERR_INVALID_ARG, "ssqa_gen_er_graph: bad n or adj");

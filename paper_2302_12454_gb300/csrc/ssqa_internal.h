@@ -156,6 +156,11 @@ bool tcs_supported(const TcImage &img, const AnnealArgs &a, std::string *why);
 size_t tcs_scratch_bytes(const TcImage &img, const AnnealArgs &a);
 int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *scratch, void *stream);
 
+// Bound, in SM clocks, of every wait a tensor-core kernel makes for the
+// tensor cores, a copy or another warp (ssqa_set_wait_limit; default 8e9,
+// about 4 s at 2 GHz).
+long long wait_limit_clocks();
+
 // Current device has compute capability 10.x (sm_100 family).
 int check_device(int *device);
 

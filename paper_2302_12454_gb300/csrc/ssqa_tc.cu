@@ -188,6 +188,7 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.smem_h = L.smem_h;
     p.smem_e = L.smem_e;
     p.smem_bar = L.smem_bar;
+    p.wait_clocks = wait_limit_clocks();
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int *err = nullptr;

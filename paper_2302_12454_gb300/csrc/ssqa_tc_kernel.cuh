@@ -52,7 +52,9 @@ constexpr int kMaxG = 8;                 // 16-spin granules per epilogue thread
 constexpr int kMaxW = 4;                 // 32-spin words per epilogue thread
 constexpr uint32_t kSignPair = 0x80008000u;
 constexpr int kMaxNh = 16;
-constexpr long long kWaitCycles = 8000000000LL;  // bounded waits: 8e9 SM clocks (about 4 s)
+// Waits for the kernel's own operations in flight (MMAs, copies) before it
+// exits after an abort: always this bound, whatever the caller's limit.
+constexpr long long kDrainCycles = 4000000000LL;
 
 struct TcParams {
     AnnealArgs a;
@@ -67,6 +69,7 @@ struct TcParams {
     float bias;                // counter offset of the FP16 epilogue
     int32_t i0_levels, i0_mult, i0_tau;  // I0 schedule (1 level: fixed I0)
     int32_t smem_A, smem_B, smem_slot, smem_h, smem_e, smem_bar;
+    long long wait_clocks;     // bound of every wait for the tensor cores (SM clocks)
     int *err;
 };
 
@@ -88,14 +91,36 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for phase `parity` of an mbarrier; false after kWaitCycles.  The bound
-// uses the SM clock counter: reading it costs no more than an ALU op, where a
-// global-timer read on every poll slowed pipelines that wait once per stage.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Limits below this many clocks are honoured by polling without suspending.
+constexpr long long kPollBelow = 1LL << 20;
+// Wait for phase `parity` of an mbarrier; false after `limit` SM clocks.  The
+// bound uses the SM clock counter: reading it costs no more than an ALU op,
+// where a global-timer read on every poll slowed pipelines that wait once per
+// stage.  try_wait may suspend the thread until the phase completes (for a
+// hardware-defined time), which would overrun a short limit: those poll with
+// test_wait instead.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    if (limit < kPollBelow) {
+        const long long t0 = clock64();
+        while (!mbar_test_wait(bar, parity))
+            if (clock64() - t0 > limit) return false;
+        return true;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 __device__ __forceinline__ void fence_mbar_init() {
@@ -248,6 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + p.smem_bar);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3);
+    uint64_t *drain = bars + 4;                        // completion of every MMA issued, before exit
     uint4 *xph = reinterpret_cast<uint4 *>(bars + 8);  // [32] noise words of the issuing warp's lanes
 
     const AnnealArgs &a = p.a;
@@ -271,6 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
+        mbar_init(drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -482,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
             const uint32_t TOP2 = h2u(__floats2half2_rn(p.bias + i0f, p.bias + i0f));
             bool waited1 = false;
             auto wait_bar = [&](int ch) {
-                if (!mbar_wait(&bars[ch], parity)) {
+                if (!mbar_wait(&bars[ch], parity, p.wait_clocks)) {
                     *abort_flag = 1;
                     atomicExch(p.err, 1);
                 }
@@ -709,7 +736,7 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 if (gg >= p.G) break;
                 const bool ch1 = p.nchunk > 1 && gg * 16 >= p.crow[0];
                 if (!(ch1 ? waited1 : waited0)) {
-                    if (!mbar_wait(&bars[ch1 ? 1 : 0], parity)) {
+                    if (!mbar_wait(&bars[ch1 ? 1 : 0], parity, p.wait_clocks)) {
                         *abort_flag = 1;
                         atomicExch(p.err, 1);
                     }
@@ -778,6 +805,11 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
                 a.best_cycle[gcol] = best_cycle;
             }
         }
+    }
+    // after an abort MMAs may still run: they complete before TMEM is freed
+    if (mma_warp && lane == 0) {
+        mma_commit(drain);
+        mbar_wait(drain, 0u, kDrainCycles);
     }
     tc_fence_before();
     __syncthreads();

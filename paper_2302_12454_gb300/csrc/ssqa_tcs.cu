@@ -70,6 +70,7 @@ struct SParams {
     int *err;
     int32_t N16, KB, NCH, L, CS, Tb, jm, last_rows;
     int32_t dual;           // a CTA serves two column groups (one accumulator buffer each)
+    long long wait_clocks;  // bound of every wait for copies, MMAs or other warps (SM clocks)
     uint32_t NR2, JM2;
     float bias;
     int32_t i0_levels, i0_mult, i0_tau;
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     if (m > 0 && *reinterpret_cast<volatile int *>(p.err)) abort_run = true;
                     for (int kb = 0; kb < p.KB && !abort_run; kb += kKps) {
                         const int nkb = p.KB - kb < kKps ? p.KB - kb : kKps;
-                        if (!mbar_wait(&empty[ps], uint32_t(pph))) {
+                        if (!mbar_wait(&empty[ps], uint32_t(pph), p.wait_clocks)) {
                             atomicExch(p.err, 1);
                             abort_run = true;
                             break;
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     const uint32_t idesc = (1u << 4) | (uint32_t(rows >> 3) << 17) | (uint32_t(128 >> 4) << 24);
                     if (m > 0 && *reinterpret_cast<volatile int *>(p.err)) abort_run = true;
                     // the epilogue has read this buffer's previous accumulators
-                    if (abort_run || !mbar_wait(&tempty[b], (mt_ph >> b) & 1u)) {
+                    if (abort_run || !mbar_wait(&tempty[b], (mt_ph >> b) & 1u, p.wait_clocks)) {
                         if (!abort_run) atomicExch(p.err, 1);
                         abort_run = true;
                         break;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     tc_fence_after();
                     for (int kb = 0; kb < p.KB; kb += kKps) {
                         const int nkb = p.KB - kb < kKps ? p.KB - kb : kKps;
-                        if (!mbar_wait(&full[ms], uint32_t(mph))) {
+                        if (!mbar_wait(&full[ms], uint32_t(mph), p.wait_clocks)) {
                             atomicExch(p.err, 1);
                             abort_run = true;
                             break;
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     for (int g = 0; g < 8; ++g) gran_loads(g, pis[g], pnu[g]);
                 }
                 if (gi == 0) {  // the chunk's accumulators (of both groups)
-                    const bool ok = mbar_wait(&tfull[b], (et_ph >> b) & 1u);
+                    const bool ok = mbar_wait(&tfull[b], (et_ph >> b) & 1u, p.wait_clocks);
                     if (__any_sync(0xffffffffu, !ok)) {
                         if (lane == 0) atomicExch(p.err, 1);
                         abort_run = true;
@@ -507,12 +508,12 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
     if (warp == 0 && lane == 0) {
         for (int s = 0; s < kStages && uint32_t(s) < nis; ++s) {
             const uint32_t last = (nis - 1u - uint32_t(s)) / uint32_t(kStages);
-            mbar_wait(&full[s], last & 1u);
+            mbar_wait(&full[s], last & 1u, kDrainCycles);
         }
     }
     if (warp == 1 && lane == 0) {
         mma_commit(drain);
-        mbar_wait(drain, 0u);
+        mbar_wait(drain, 0u, kDrainCycles);
     }
     tc_fence_before();
     __syncthreads();
@@ -692,6 +693,7 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
         std::memcpy(&p.JM2, &j, 4);
     }
     p.bias = 1152.f;
+    p.wait_clocks = wait_limit_clocks();
     p.i0_levels = 1;
     p.i0_mult = 2;
     p.i0_tau = 1 << 30;

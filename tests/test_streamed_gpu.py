@@ -207,3 +207,31 @@ def test_two_column_groups_per_cta():
         o = O.anneal(h, J, R=R, cycles=cycles, trials=1, seed=43, tau=2, trial_offset=tr, track_best=True)
         for k in ("sigma", "Is", "E_final", "E_best", "best_cycle"):
             np.testing.assert_array_equal(g[k][tr], o[k][0], err_msg=f"{k} trial {tr}")
+
+
+@pytest.mark.parametrize("kind,start", [("large_gi_n50", 4799), ("sk_n8192", 1998)])
+def test_late_anneal_against_oracle(kind, start):
+    """The late regime of the large configurations: one trial resumed from the
+    GPU's own state at cycle 4799 (config 3, 5000 cycles) or 1998 (config 4,
+    2000 cycles), two more cycles on both sides.  Those cycles run at Table 2's
+    top J_perp level (t mod tau (beta + 1) = 399 / 398 with tau = 100) and, for
+    config 3, across the level's reset at t = 4800; counters are saturated and
+    few spins flip."""
+    c = W.CONFIGS[kind]
+    if c["kind"] == "gi":
+        I = gi(c["n"], c["p"], c["graph_seed"], c["perm_seed"])
+    else:
+        I = S.Ising.dense(W.sk_couplings(c["N"], c["j_seed"]), np.zeros(c["N"], np.int32))
+    h, J, _ = I.export()
+    tr = 3
+    kw = dict(R=c["R"], trials=1, seed=c["seed"], tau=c["tau"], trial_offset=tr)
+    first = S.anneal(I, cycles=start, want_hist=True, algo=S.ALGO_AUTO, **kw)
+    nxt = S.anneal(I, cycles=2, want_hist=True, algo=S.ALGO_AUTO, init_mode=S.INIT_FROM_STATE, start_cycle=start,
+                   state=first, track_best=True, **kw)
+    st = dict(sigma=first["sigma"], Is=first["Is"], hist=first["hist"])
+    o = O.anneal(h, J, cycles=2, init_mode=2, start_cycle=start, state=st, track_best=True, **kw)
+    for k in ("sigma", "Is", "E_final", "E_best", "best_cycle", "hist"):
+        np.testing.assert_array_equal(nxt[k], o[k], err_msg=k)
+    # the state is the late regime: counters mostly saturated
+    sat = np.isin(first["Is"], (-24, 23)).mean()
+    assert sat > 0.5, sat
