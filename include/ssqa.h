@@ -221,6 +221,29 @@ typedef struct ssqa_result {
 int ssqa_anneal(const ssqa_ising *ising, const ssqa_params *params, ssqa_result *out,
                 void *cuda_stream);
 
+/* Several independent anneals (Eq. 6 per problem) submitted together: the
+ * problems the resident tensor-core kernel takes, of uneven size, cycle
+ * count, replica and trial count, seed and instance, run as the column
+ * groups of one launch of that kernel (at most 48 problems per launch; one
+ * launch per kernel variant: counter format, replica exchange, accumulator,
+ * coupling and energy tracking), each CTA with its own problem's
+ * parameters.  Batched launches exist for replica delay d = 1 with R dividing
+ * 32 (Table 2's d); other problems, and problems for the streamed or
+ * CUDA-core paths, run one launch each.  Every problem's result is
+ * bit-identical to ssqa_anneal with the same arguments.  Not in the paper,
+ * which runs one anneal at a time.
+ *   count: problems; isings, params, outs: count entries each, as for
+ *   ssqa_anneal; every params[i].flags must include SSQA_FLAG_DEVICE_PTRS
+ *   (outs hold device pointers).  The call returns when every problem has
+ *   completed on cuda_stream.
+ *   launches (may be NULL): receives the number of kernel launches made
+ *   (a problem on the streamed or CUDA-core paths may launch more than one
+ *   kernel but counts once).
+ * Errors: as ssqa_anneal, for the first problem that fails (problems before
+ * it may have run). */
+int ssqa_anneal_batch(int32_t count, const ssqa_ising *const *isings, const ssqa_params *params,
+                      ssqa_result *outs, int32_t *launches, void *cuda_stream);
+
 /* The kernel path ssqa_anneal takes for this instance and these parameters,
  * decided on the host without running anything (no GPU needed).  Not in the
  * paper: it exposes the library's choice between its exact paths for Eq. 6

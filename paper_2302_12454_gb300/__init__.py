@@ -72,6 +72,8 @@ def lib():
         L.ssqa_anneal.argtypes = [vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
         L.ssqa_energy.argtypes = [vp, vp, i64, vp, u32, vp]
         L.ssqa_plan.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_char_p, ctypes.c_size_t]
+        L.ssqa_anneal_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Params), ctypes.POINTER(Result),
+                                        ctypes.POINTER(i32), vp]
         L.ssqa_anneal_noalloc.argtypes = [i32, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Result), vp]
         L.ssqa_set_wait_limit.argtypes = [i64]
         L.ssqa_tts.argtypes = [ctypes.c_double] * 3
@@ -264,6 +266,34 @@ def plan(ising: Ising, *, R: int, cycles: int, trials: int, seed: int = 0, track
     buf = ctypes.create_string_buffer(512)
     rc = _check(lib().ssqa_plan(ising.handle, ctypes.byref(p), buf, 512), "plan")
     return rc, buf.value.decode()
+
+
+def anneal_batch(items, stream=None) -> int:
+    """Several device-buffer anneals in as few launches as possible
+    (ssqa_anneal_batch).  items: list of (ising, params, buffers) with buffers a
+    dict of torch CUDA tensors (sigma, Is, and optionally hist, e_final,
+    e_best, best_cycle, e_trace).  Returns the number of kernel launches."""
+    import torch
+
+    n = len(items)
+    isings = (ctypes.c_void_p * n)(*[it[0].handle.value for it in items])
+    ps = (Params * n)()
+    rs = (Result * n)()
+    for k, (ising, params, buf) in enumerate(items):
+        p = Params.from_buffer_copy(params)
+        p.flags |= FLAG_DEVICE_PTRS
+        if buf.get("e_best") is not None:
+            p.flags |= FLAG_TRACK_BEST
+        ps[k] = p
+        rs[k] = Result(_ptr(buf["sigma"]), _ptr(buf.get("hist")), _ptr(buf["Is"]), _ptr(buf.get("e_final")),
+                       _ptr(buf.get("e_best")), _ptr(buf.get("best_cycle")), _ptr(buf.get("e_trace")))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    launches = ctypes.c_int32()
+    _check(lib().ssqa_anneal_batch(n, isings, ps, rs, ctypes.byref(launches), ctypes.c_void_p(handle)),
+           "anneal_batch")
+    return launches.value
 
 
 def energy(ising: Ising, sigma) -> np.ndarray:

@@ -13,6 +13,7 @@
 #include <memory>
 #include <new>
 #include <numeric>
+#include <vector>
 
 #include "ssqa_internal.h"
 
@@ -755,6 +756,55 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
         if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "ssqa_anneal");
     }
     if ((e = cudaGetLastError())) return cuda_fail(e, "ssqa_anneal");
+    return SSQA_OK;
+}
+
+extern "C" int ssqa_anneal_batch(int32_t count, const ssqa_ising *const *isings, const ssqa_params *params,
+                                 ssqa_result *outs, int32_t *launches, void *stream) {
+    if (launches) *launches = 0;
+    if (count < 0 || (count > 0 && (!isings || !params || !outs)))
+        return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_batch: bad count or NULL array");
+    std::vector<TcBatchItem> batch;
+    std::vector<int> single;
+    batch.reserve(size_t(count));
+    for (int32_t i = 0; i < count; ++i) {
+        const ssqa_ising *I = isings[i];
+        const ssqa_params *p = &params[i];
+        int rc = validate(I, p, &outs[i]);
+        if (rc) return rc;
+        if (!(p->flags & SSQA_FLAG_DEVICE_PTRS))
+            return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_batch: every item needs SSQA_FLAG_DEVICE_PTRS");
+        DeviceCopy *dc = nullptr;
+        if ((rc = device_copy(I, &dc))) return rc;
+        AnnealArgs a = make_args(I, p);
+        a.J = dc->J;
+        a.J_pad = dc->J_pad;
+        a.Np = dc->Np;
+        a.h = dc->h;
+        a.sigma = outs[i].sigma;
+        a.hist = p->delay ? outs[i].sigma_hist : nullptr;
+        a.Is = outs[i].is_state;
+        a.e_final = outs[i].e_final;
+        a.e_best = a.track_best ? outs[i].e_best : nullptr;
+        a.best_cycle = a.track_best ? outs[i].best_cycle : nullptr;
+        a.e_trace = outs[i].e_trace;
+        int algo = SSQA_ALGO_AUTO;
+        std::string desc;
+        if ((rc = choose_path(I, p, a, &algo, &desc))) return rc;
+        if (algo == SSQA_ALGO_TENSOR)
+            batch.push_back(TcBatchItem{&I->tc, dc, a});
+        else
+            single.push_back(i);
+    }
+    int n = 0;
+    if (!batch.empty()) {
+        if (int rc = tc_anneal_batch(batch.data(), int(batch.size()), &n, stream)) return rc;
+    }
+    for (int i : single) {
+        if (int rc = ssqa_anneal(isings[i], &params[i], &outs[i], stream)) return rc;
+        ++n;
+    }
+    if (launches) *launches = n;
     return SSQA_OK;
 }
 

@@ -133,6 +133,16 @@ struct TcVariant {
 };
 TcVariant tc_variant(const TcImage &img, const AnnealArgs &a);
 int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream);
+// Several resident-kernel problems: those of one kernel variant run in one
+// launch (or a few, 48 problems at most per launch), the others alone; all on
+// `stream`, complete on return.  *launches (if non-NULL) is incremented per
+// kernel launch.
+struct TcBatchItem {
+    const TcImage *img;
+    const DeviceCopy *dc;
+    AnnealArgs a;
+};
+int tc_anneal_batch(const TcBatchItem *items, int count, int *launches, void *stream);
 
 // I0 of cycle t: fixed, or the SSA schedule of Sec. 4.4.
 inline int32_t i0_at(const AnnealArgs &a, int64_t t) {

@@ -6,6 +6,9 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <memory>
+#include <new>
+#include <vector>
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -139,11 +142,14 @@ TcVariant tc_variant(const TcImage &img, const AnnealArgs &a) {
     return v;
 }
 
-int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream) {
-    Layout L;
+// Kernel parameters, shared-memory layout and variant of one problem (no
+// device work); SSQA_ERR_UNSUPPORTED when the resident kernel cannot take it.
+static int build_params(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, TcParams *pp, Layout *Lp,
+                        TcVariant *vp) {
+    Layout &L = *Lp;
     std::string why;
     if (!plan(img, a, &L, &why)) return fail(SSQA_ERR_UNSUPPORTED, "tensor path: " + why);
-    TcParams p;
+    TcParams &p = *pp;
     std::memset(&p, 0, sizeof(p));
     p.a = a;
     p.b_img = dc.tc_b;
@@ -161,7 +167,8 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.crow[0] = img.chunk_rows[0];
     p.crow[1] = img.chunk_rows[1];
     const TcVariant var = tc_variant(img, a);
-    const bool fast = var.bytes, shfl = var.shfl, f16 = var.f16;
+    *vp = var;
+    const bool fast = var.bytes, f16 = var.f16;
     for (int ch = 0; ch < 2; ++ch) {
         // instruction descriptor, kind::f8f6f4: D f16 (bits 4-5 = 0) or f32 (1),
         // A and B E4M3 (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -189,14 +196,21 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     p.smem_e = L.smem_e;
     p.smem_bar = L.smem_bar;
     p.wait_clocks = wait_limit_clocks();
+    return SSQA_OK;
+}
 
+int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *stream) {
+    Layout L;
+    TcParams p;
+    TcVariant var;
+    if (int rc = build_params(img, dc, a, &p, &L, &var)) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int *err = nullptr;
     cudaError_t e = dev_alloc(reinterpret_cast<void **>(&err), sizeof(int), st);
     if (e) return fail(SSQA_ERR_OOM, std::string("tensor path: ") + cudaGetErrorString(e));
     cudaMemsetAsync(err, 0, sizeof(int), st);
     p.err = err;
-    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, fast, f16, shfl);
+    KernelFn fn = pick(a.delay, a.both != 0, a.track_best, var.bytes, var.f16, var.shfl);
     configure_once(fn);
     const int64_t grid = (int64_t(a.trials) + L.Tb - 1) / L.Tb;
     fn<<<unsigned(grid), kThreads, L.total, st>>>(p);
@@ -207,6 +221,73 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     cudaFreeAsync(err, st);
     if (e) return fail(SSQA_ERR_DEVICE, std::string("tensor path kernel: ") + cudaGetErrorString(e));
     if (herr) return fail(SSQA_ERR_TIMEOUT, "tensor path: a bounded wait for the tensor cores timed out");
+    return SSQA_OK;
+}
+
+int tc_anneal_batch(const TcBatchItem *items, int count, int *launches, void *stream) {
+    using namespace tc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<TcParams> ps(count);
+    std::vector<Layout> Ls(count);
+    std::vector<BatchFn> fns(count);
+    std::vector<std::pair<BatchFn, int>> order;  // batchable items grouped by kernel variant
+    for (int i = 0; i < count; ++i) {
+        TcVariant var;
+        if (int rc = build_params(*items[i].img, *items[i].dc, items[i].a, &ps[i], &Ls[i], &var)) return rc;
+        const AnnealArgs &a = items[i].a;
+        fns[i] = pick_batch(a.delay, a.both != 0, a.track_best, var.bytes, var.f16, var.shfl);
+        if (fns[i]) order.emplace_back(fns[i], i);
+    }
+    // variants without a batched kernel run alone
+    for (int i = 0; i < count; ++i)
+        if (!fns[i]) {
+            if (int rc = tc_anneal(*items[i].img, *items[i].dc, items[i].a, stream)) return rc;
+            if (launches) ++*launches;
+        }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<BatchFn, int> &x, const std::pair<BatchFn, int> &y) {
+                         return reinterpret_cast<uintptr_t>(x.first) < reinterpret_cast<uintptr_t>(y.first);
+                     });
+    int *err = nullptr;
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&err), sizeof(int), st);
+    if (e) return fail(SSQA_ERR_OOM, std::string("tensor path: ") + cudaGetErrorString(e));
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    std::unique_ptr<TcBatch> b(new (std::nothrow) TcBatch());
+    if (!b) {
+        cudaFreeAsync(err, st);
+        return fail(SSQA_ERR_OOM, "tensor path: out of host memory");
+    }
+    size_t k = 0;
+    while (!e && k < order.size()) {
+        // one launch: consecutive items of one variant, at most kMaxBatch
+        const BatchFn fn = order[k].first;
+        std::memset(b.get(), 0, sizeof(TcBatch));
+        int smem = 0;
+        int64_t ctas = 0;
+        while (k < order.size() && order[k].first == fn && b->count < kMaxBatch) {
+            const int i = order[k].second;
+            TcParams &p = ps[i];
+            p.err = err;
+            const int64_t grid = (int64_t(items[i].a.trials) + Ls[i].Tb - 1) / Ls[i].Tb;
+            b->first[b->count] = int32_t(ctas);
+            b->items[b->count] = p;
+            ++b->count;
+            ctas += grid;
+            smem = std::max(smem, Ls[i].total);
+            ++k;
+        }
+        b->first[b->count] = int32_t(ctas);
+        configure_once(reinterpret_cast<KernelFn>(fn));
+        fn<<<unsigned(ctas), kThreads, smem, st>>>(*b);
+        e = cudaGetLastError();
+        if (!e && launches) ++*launches;
+    }
+    int herr = 0;
+    if (!e) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(err, st);
+    if (e) return fail(SSQA_ERR_DEVICE, std::string("batched tensor path kernel: ") + cudaGetErrorString(e));
+    if (herr) return fail(SSQA_ERR_TIMEOUT, "batched tensor path: a bounded wait for the tensor cores timed out");
     return SSQA_OK;
 }
 

@@ -261,8 +261,9 @@ __device__ __forceinline__ uint32_t word_bit(uint32_t w, uint32_t i) { return (w
 // kF16 (byte counters only): the accumulator is FP16 (every partial sum is an
 // integer of magnitude <= 2048, exact in FP16), read from TMEM as packed half2
 // pairs, so the epilogue needs no FP32 -> FP16 conversion.
+// One CTA's whole anneal: column group `cta` of the problem described by p.
 template <int D, bool kBoth, bool kTrack, bool kFast, bool kF16, bool kShfl>
-__global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_constant__ TcParams p) {
+__device__ __forceinline__ void cta_anneal(const TcParams &p, const int cta) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = sm + p.smem_A;
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     // it is the warp of the last part, which owns the fewest spin words.
     const bool mma_warp = warp == kEpiWarps - 1;
     const int Kp = p.Kp;
-    const int64_t trial0 = int64_t(blockIdx.x) * p.Tb;
+    const int64_t trial0 = int64_t(cta) * p.Tb;
     const int ntr = int(a.trials - trial0 < p.Tb ? a.trials - trial0 : p.Tb);
     const int vcols = ntr * a.R;
     const int64_t col0 = trial0 * a.R;  // global column of local column 0
@@ -819,7 +820,35 @@ __global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_const
     }
 }
 
+template <int D, bool kBoth, bool kTrack, bool kFast, bool kF16, bool kShfl>
+__global__ void __launch_bounds__(kThreads, 1) ssqa_tc_kernel(const __grid_constant__ TcParams p) {
+    cta_anneal<D, kBoth, kTrack, kFast, kF16, kShfl>(p, blockIdx.x);
+}
+
+// Several problems in one launch: item i owns CTAs [first[i], first[i + 1]),
+// one per 128-column group of its trials, each running cta_anneal with the
+// item's own parameters (instance, sizes, cycles, seed, buffers).  The items
+// share the kernel variant; their shared-memory layouts fit the launch's
+// dynamic size (the largest of them).
+constexpr int kMaxBatch = 48;
+struct TcBatch {
+    int32_t count;
+    int32_t first[kMaxBatch + 1];
+    TcParams items[kMaxBatch];
+};
+static_assert(sizeof(TcBatch) <= 32764, "kernel parameters are limited to 32764 bytes");
+template <int D, bool kBoth, bool kTrack, bool kFast, bool kF16, bool kShfl>
+__global__ void __launch_bounds__(kThreads, 1) ssqa_tc_batch_kernel(const __grid_constant__ TcBatch b) {
+    int it = 0;
+    while (it + 1 < b.count && int(blockIdx.x) >= b.first[it + 1]) ++it;
+    cta_anneal<D, kBoth, kTrack, kFast, kF16, kShfl>(b.items[it], int(blockIdx.x) - b.first[it]);
+}
+
 using KernelFn = void (*)(TcParams);
+using BatchFn = void (*)(TcBatch);
+// Batched launches exist for the shuffle-exchange variants with delay d = 1
+// (Table 2's d, replica counts dividing 32); nullptr for other variants.
+BatchFn pick_batch(int d, bool both, bool track, bool bytes, bool f16, bool shfl);
 
 // Kernel variants are split over several translation units (per delay d, and
 // shuffle vs shared-memory-slot exchange) so that they compile in parallel.

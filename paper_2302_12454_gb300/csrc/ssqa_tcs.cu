@@ -717,6 +717,10 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
     if (CS > 8) CS = 8;
     if (CS > p.NCH) CS = p.NCH;
     if (CS < 1) CS = 1;
+    // the cycle takes as long as the rank with the most chunks: the smallest
+    // cluster with that many chunks per rank does the same work on fewer SMs
+    // (10 chunks: 5 CTAs of 2 chunks, not 8 CTAs of 1 or 2)
+    while (CS > 1 && (p.NCH + CS - 2) / (CS - 1) == (p.NCH + CS - 1) / CS) --CS;
     uint8_t *q = static_cast<uint8_t *>(scratch);
     p.A = q;
     q += up256(size_t(groups) * p.L * p.KB * kABytes);
