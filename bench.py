@@ -423,12 +423,14 @@ def run_ours(args, rank, world):
     }
     if rank == 0:
         out["clocks"] = clk.summary(int(os.environ.get("LOCAL_RANK", 0)))
-        # served latency: a seeded Poisson stream of GI requests (a bounded
-        # sample of the serving workload: n in [8, 20], R = 16, 32 trials)
+        # served latency: a seeded Poisson stream of GI requests with the
+        # serving workload's distributions (n in [8, 50], i.e. 64 to 2500
+        # spins, p in [0.3, 0.7], R = 16, 32 trials, cycles in {1000, 2000,
+        # 5000}); 400 requests, a bounded sample of its 10 000
         from paper_2302_12454_gb300 import serving_bench as SB
 
-        out["served"] = SB.run(S, W, count=64, n_min=8, n_max=20, cycles_set=(500, 1000, 2000), slots=32,
-                               plain_sample=8)
+        out["served"] = SB.run(S, W, count=400, n_min=8, n_max=50, cycles_set=(1000, 2000, 5000), slots=32,
+                               plain_sample=16, seq_sample=100, capacity_sample=200)
         out["rows"] = row_timings(S, torch, stream, I, cfg, sigma, Is, E, ms_per_step)
         pool = None if args.no_cpu_baseline else OraclePool(min(64, os.cpu_count() or 1))
         if not args.no_large:

@@ -5,6 +5,7 @@ served latency.
       [--cycles C] [--trials T] [--algo tensor|plain|delta|auto] [--repeat K]
   python -m paper_2302_12454_gb300 serve-bench [--requests 200] [--n-min 8]
       [--n-max 20] [--cycles 1000,2000,5000] [--slots 32] [--load 0.8]
+      [--seq-sample 200] [--capacity-sample 400] [--plain-sample 16]
 
 Prints one line per run: device time of the anneal (CUDA events on the
 launching stream), spin-updates/s, success probability P_s (any replica at
@@ -78,7 +79,9 @@ def cmd_serve(args):
 
     B.build()
     out = SB.run(S, W, count=args.requests, n_min=args.n_min, n_max=args.n_max,
-                 cycles_set=tuple(int(c) for c in args.cycles.split(",")), slots=args.slots, load=args.load)
+                 cycles_set=tuple(int(c) for c in args.cycles.split(",")), slots=args.slots, load=args.load,
+                 seq_sample=args.seq_sample, capacity_sample=args.capacity_sample, plain_sample=args.plain_sample,
+                 build_threads=args.build_threads)
     print(_json.dumps(out), flush=True)
 
 
@@ -123,6 +126,10 @@ def main(argv=None):
     sv.add_argument("--cycles", default="1000,2000,5000")
     sv.add_argument("--slots", type=int, default=32)
     sv.add_argument("--load", type=float, default=0.8)
+    sv.add_argument("--seq-sample", type=int, default=200, help="requests timed one at a time")
+    sv.add_argument("--capacity-sample", type=int, default=400, help="requests of the closed-loop capacity run")
+    sv.add_argument("--plain-sample", type=int, default=16, help="requests timed on the plain path")
+    sv.add_argument("--build-threads", type=int, default=8, help="threads building instances ahead of arrival")
     sw = sub.add_parser("sweep", help="P_s / TTS sweep on synthetic GI (Table 4 sizes or Table 3 cases) on cuda:0")
     sw.add_argument("--table", type=int, default=4, choices=[3, 4])
     sw.add_argument("--trials", type=int, default=100)

@@ -272,7 +272,7 @@ ssqa_ising *new_ising(int32_t N) {
 }
 }  // namespace
 
-int device_copy(const ssqa_ising *cI, DeviceCopy **out) {
+int device_copy(const ssqa_ising *cI, DeviceCopy **out, cudaStream_t st) {
     ssqa_ising *I = const_cast<ssqa_ising *>(cI);
     int dev = 0;
     int rc = check_device(&dev);
@@ -283,43 +283,52 @@ int device_copy(const ssqa_ising *cI, DeviceCopy **out) {
         *out = &it->second;
         return SSQA_OK;
     }
+    // Stream-ordered allocations from the library pool and copies on the
+    // caller's stream, completed before the copy is published (other streams
+    // may use it next); ssqa_ising_free returns them with cudaFreeAsync.
+    // Neither allocation nor release synchronises the device, so instances can
+    // come and go while other anneals run (a server's requests).
     DeviceCopy dc;
     const size_t N = size_t(I->N);
+    std::vector<void *> got;
     auto bad = [&](cudaError_t e) {
-        cudaFree(dc.J);
-        cudaFree(dc.J_pad);
-        cudaFree(dc.h);
-        cudaFree(dc.tc_b);
-        cudaFree(dc.tc_h_unit);
-        cudaFree(dc.tcs_b);
-        cudaFree(dc.tcs_hf);
+        for (void *q : got) cudaFreeAsync(q, st);
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? SSQA_ERR_OOM : SSQA_ERR_DEVICE,
                     std::string("instance upload: ") + cudaGetErrorString(e));
     };
+    auto alloc = [&](void **q, size_t bytes) {
+        cudaError_t e = dev_alloc(q, bytes ? bytes : 1, st);
+        if (!e) got.push_back(*q);
+        return e;
+    };
     cudaError_t e;
-    if ((e = cudaMalloc(&dc.J, N * N))) return bad(e);
-    if ((e = cudaMalloc(&dc.h, N * 4))) return bad(e);
-    if ((e = cudaMemcpy(dc.J, I->J.data(), N * N, cudaMemcpyHostToDevice))) return bad(e);
     dc.Np = int32_t((N + 15) / 16 * 16);
-    if ((e = cudaMalloc(&dc.J_pad, N * dc.Np))) return bad(e);
-    if ((e = cudaMemset(dc.J_pad, 0, N * dc.Np))) return bad(e);
-    if ((e = cudaMemcpy2D(dc.J_pad, dc.Np, I->J.data(), N, N, N, cudaMemcpyHostToDevice))) return bad(e);
-    if ((e = cudaMemcpy(dc.h, I->h.data(), N * 4, cudaMemcpyHostToDevice))) return bad(e);
+    if ((e = alloc(reinterpret_cast<void **>(&dc.J), N * N))) return bad(e);
+    if ((e = alloc(reinterpret_cast<void **>(&dc.h), N * 4))) return bad(e);
+    if ((e = alloc(reinterpret_cast<void **>(&dc.J_pad), N * dc.Np))) return bad(e);
+    if ((e = cudaMemcpyAsync(dc.J, I->J.data(), N * N, cudaMemcpyHostToDevice, st))) return bad(e);
+    if ((e = cudaMemsetAsync(dc.J_pad, 0, N * dc.Np, st))) return bad(e);
+    if ((e = cudaMemcpy2DAsync(dc.J_pad, dc.Np, I->J.data(), N, N, N, cudaMemcpyHostToDevice, st))) return bad(e);
+    if ((e = cudaMemcpyAsync(dc.h, I->h.data(), N * 4, cudaMemcpyHostToDevice, st))) return bad(e);
+    std::vector<float> hf;
     if (I->tc.s_ok) {
-        if ((e = cudaMalloc(&dc.tcs_b, I->tc.bs.size()))) return bad(e);
-        if ((e = cudaMemcpy(dc.tcs_b, I->tc.bs.data(), I->tc.bs.size(), cudaMemcpyHostToDevice))) return bad(e);
-        std::vector<float> hf(N);
+        if ((e = alloc(reinterpret_cast<void **>(&dc.tcs_b), I->tc.bs.size()))) return bad(e);
+        if ((e = cudaMemcpyAsync(dc.tcs_b, I->tc.bs.data(), I->tc.bs.size(), cudaMemcpyHostToDevice, st)))
+            return bad(e);
+        hf.resize(N);
         for (size_t i = 0; i < N; ++i) hf[i] = float(I->tc.h_unit[i]);
-        if ((e = cudaMalloc(&dc.tcs_hf, N * 4))) return bad(e);
-        if ((e = cudaMemcpy(dc.tcs_hf, hf.data(), N * 4, cudaMemcpyHostToDevice))) return bad(e);
+        if ((e = alloc(reinterpret_cast<void **>(&dc.tcs_hf), N * 4))) return bad(e);
+        if ((e = cudaMemcpyAsync(dc.tcs_hf, hf.data(), N * 4, cudaMemcpyHostToDevice, st))) return bad(e);
     }
     if (I->tc.ok) {
-        if ((e = cudaMalloc(&dc.tc_b, I->tc.b.size()))) return bad(e);
-        if ((e = cudaMemcpy(dc.tc_b, I->tc.b.data(), I->tc.b.size(), cudaMemcpyHostToDevice))) return bad(e);
-        if ((e = cudaMalloc(&dc.tc_h_unit, N * 4))) return bad(e);
-        if ((e = cudaMemcpy(dc.tc_h_unit, I->tc.h_unit.data(), N * 4, cudaMemcpyHostToDevice))) return bad(e);
+        if ((e = alloc(reinterpret_cast<void **>(&dc.tc_b), I->tc.b.size()))) return bad(e);
+        if ((e = cudaMemcpyAsync(dc.tc_b, I->tc.b.data(), I->tc.b.size(), cudaMemcpyHostToDevice, st))) return bad(e);
+        if ((e = alloc(reinterpret_cast<void **>(&dc.tc_h_unit), N * 4))) return bad(e);
+        if ((e = cudaMemcpyAsync(dc.tc_h_unit, I->tc.h_unit.data(), N * 4, cudaMemcpyHostToDevice, st)))
+            return bad(e);
     }
+    if ((e = cudaStreamSynchronize(st))) return bad(e);
     auto res = I->dev.emplace(dev, dc);
     *out = &res.first->second;
     return SSQA_OK;
@@ -455,15 +464,15 @@ void ssqa_ising_free(ssqa_ising *I) {
     if (!I) return;
     int cur = 0;
     cudaGetDevice(&cur);
+    // the memory returns to the library pool in the legacy stream's order:
+    // no device-wide synchronisation (the caller guarantees no work still
+    // uses the instance)
     for (auto &kv : I->dev) {
         cudaSetDevice(kv.first);
-        cudaFree(kv.second.J);
-        cudaFree(kv.second.J_pad);
-        cudaFree(kv.second.h);
-        cudaFree(kv.second.tc_b);
-        cudaFree(kv.second.tc_h_unit);
-        cudaFree(kv.second.tcs_b);
-        cudaFree(kv.second.tcs_hf);
+        void *ps[] = {kv.second.J, kv.second.J_pad, kv.second.h, kv.second.tc_b, kv.second.tc_h_unit,
+                      kv.second.tcs_b, kv.second.tcs_hf};
+        for (void *q : ps)
+            if (q) cudaFreeAsync(q, nullptr);
     }
     cudaSetDevice(cur);
     cudaGetLastError();
@@ -652,8 +661,8 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     int rc = validate(I, p, r);
     if (rc) return rc;
     DeviceCopy *dc = nullptr;
-    if ((rc = device_copy(I, &dc))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = device_copy(I, &dc, st))) return rc;
     const bool devptr = p->flags & SSQA_FLAG_DEVICE_PTRS;
     const size_t cols = size_t(p->trials) * p->R;
     const size_t nsp = cols * I->N;
@@ -759,6 +768,20 @@ extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_resul
     return SSQA_OK;
 }
 
+namespace ssqa {
+int batch_key(const ssqa_ising *I, const ssqa_params *p) {
+    if (!I || !p || p->R < 1 || p->R > 128 || p->trials < 1 || p->beta < 1) return -1;
+    const AnnealArgs a = make_args(I, p);
+    int algo = SSQA_ALGO_AUTO;
+    std::string desc;
+    const std::string saved = g_last_error;
+    const int rc = choose_path(I, p, a, &algo, &desc);
+    g_last_error = saved;
+    if (rc || algo != SSQA_ALGO_TENSOR) return -1;
+    return tc_batch_key(I->tc, a);
+}
+}  // namespace ssqa
+
 extern "C" int ssqa_anneal_batch(int32_t count, const ssqa_ising *const *isings, const ssqa_params *params,
                                  ssqa_result *outs, int32_t *launches, void *stream) {
     if (launches) *launches = 0;
@@ -775,7 +798,7 @@ extern "C" int ssqa_anneal_batch(int32_t count, const ssqa_ising *const *isings,
         if (!(p->flags & SSQA_FLAG_DEVICE_PTRS))
             return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_batch: every item needs SSQA_FLAG_DEVICE_PTRS");
         DeviceCopy *dc = nullptr;
-        if ((rc = device_copy(I, &dc))) return rc;
+        if ((rc = device_copy(I, &dc, static_cast<cudaStream_t>(stream)))) return rc;
         AnnealArgs a = make_args(I, p);
         a.J = dc->J;
         a.J_pad = dc->J_pad;
@@ -840,7 +863,7 @@ extern "C" int ssqa_energy(const ssqa_ising *I, const int8_t *sigma, int64_t cou
     if (flags & ~uint32_t(SSQA_FLAG_DEVICE_PTRS)) return fail(SSQA_ERR_INVALID_ARG, "ssqa_energy: unknown flags");
     if (count == 0) return SSQA_OK;
     DeviceCopy *dc = nullptr;
-    int rc = device_copy(I, &dc);
+    int rc = device_copy(I, &dc, static_cast<cudaStream_t>(stream));
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;

@@ -77,8 +77,9 @@ struct ssqa_ising {
 
 namespace ssqa {
 
-// Device copy of an instance on the current device (created on first use).
-int device_copy(const ssqa_ising *ising, DeviceCopy **out);
+// Device copy of an instance on the current device (created on first use,
+// from the library pool, on stream `st`, complete when this returns).
+int device_copy(const ssqa_ising *ising, DeviceCopy **out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Launch descriptors (device pointers only)
@@ -143,6 +144,14 @@ struct TcBatchItem {
     AnnealArgs a;
 };
 int tc_anneal_batch(const TcBatchItem *items, int count, int *launches, void *stream);
+// Kernel variant of a resident-kernel problem that has a batched launch, as
+// a small non-negative key (problems with equal keys can share a launch);
+// -1 when the problem has no batched launch.
+int tc_batch_key(const TcImage &img, const AnnealArgs &a);
+// The same for a problem given by its instance and parameters (host only):
+// -1 unless ssqa_anneal would run it on the resident kernel with a batched
+// variant.
+int batch_key(const ssqa_ising *ising, const ssqa_params *params);
 
 // I0 of cycle t: fixed, or the SSA schedule of Sec. 4.4.
 inline int32_t i0_at(const AnnealArgs &a, int64_t t) {

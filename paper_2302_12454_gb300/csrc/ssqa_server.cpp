@@ -4,12 +4,18 @@
 // per-request computation (Eq. 6).
 //
 // Requests queue on the host.  `max_slots` worker threads each own a CUDA
-// stream; a worker admits the oldest queued request whose device footprint
-// fits in what is left of the HBM budget, runs it with ssqa_anneal on its
-// stream (all state device-resident for the whole anneal), and publishes the
-// result.  Requests admitted while others run overlap on the GPU.  Results
-// are identical to a lone ssqa_anneal call: every random draw is keyed by the
-// request's own seed and trial indices.
+// stream.  A worker admits the oldest queued request whose device footprint
+// fits in what is left of the HBM budget; a request may be passed over only a
+// bounded number of times (2 x max_slots), after which nothing behind it is
+// admitted until it fits, so that a large request cannot starve.  When the
+// admitted request runs on the resident tensor-core kernel with a batched
+// variant, the worker also takes the queued requests of the same variant and
+// cycle count that fit (up to one wave of CTAs) and runs them all in one
+// launch (ssqa_anneal_batch); other requests run alone (ssqa_anneal).  All
+// state stays on the device for the whole anneal; requests admitted while
+// others run overlap on the GPU.  Results are identical to a lone
+// ssqa_anneal call: every random draw is keyed by the request's own seed and
+// trial indices.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -34,6 +40,9 @@ struct Request {
     const ssqa_ising *ising = nullptr;
     ssqa_params params{};
     size_t bytes = 0;
+    int key = -1;     // batched launch variant (-1: runs alone)
+    int ctas = 0;     // column groups = CTAs on the resident kernel
+    int bypass = 0;   // times a later request was admitted while this one was the oldest
     int state = 0;  // 0 queued, 1 running, 2 done
     int rc = SSQA_OK;
     std::string err;
@@ -69,35 +78,82 @@ struct ssqa_server {
     bool stop = false;
     std::vector<std::thread> workers;
 
+    int nsm = 148;
+    int max_bypass = 8;
+
+    // Under mu: the requests to run next (oldest first, bounded bypass), or
+    // none.  A batch shares one launch: same variant and cycle count, at most
+    // one wave of CTAs, at most ssqa's batch size.
+    std::vector<std::shared_ptr<Request>> admit() {
+        std::vector<std::shared_ptr<Request>> out;
+        if (queue.empty()) return out;
+        size_t free = budget - used;
+        int ctas = 0;
+        const uint64_t head_ticket = queue.front()->ticket;
+        for (auto it = queue.begin(); it != queue.end();) {
+            Request &q = **it;
+            const bool head = q.ticket == head_ticket;
+            bool take = q.bytes <= free;
+            if (take && !out.empty()) {
+                const Request &first = *out.front();
+                take = first.key >= 0 && q.key == first.key && q.params.cycles == first.params.cycles &&
+                       ctas + q.ctas <= nsm && out.size() < 48;
+            }
+            if (take) {
+                free -= q.bytes;
+                ctas += q.ctas;
+                out.push_back(*it);
+                it = queue.erase(it);
+                if (out.front()->key < 0) break;  // runs alone
+                continue;
+            }
+            if (head && out.empty()) {
+                // the oldest request does not fit: later ones may pass it a bounded number of times
+                if (q.bypass >= max_bypass) break;
+            }
+            ++it;
+        }
+        if (!out.empty() && !queue.empty()) {
+            // the oldest request left was passed over if anything newer was admitted
+            uint64_t newest = 0;
+            for (const auto &r : out) newest = r->ticket > newest ? r->ticket : newest;
+            if (queue.front()->ticket < newest) ++queue.front()->bypass;
+        }
+        return out;
+    }
+
     void worker() {
         cudaSetDevice(device);
         cudaStream_t st = nullptr;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         for (;;) {
-            std::shared_ptr<Request> r;
+            std::vector<std::shared_ptr<Request>> rs;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 for (;;) {
                     if (stop && queue.empty()) break;
-                    for (auto it = queue.begin(); it != queue.end(); ++it)
-                        if (used + (*it)->bytes <= budget) {
-                            r = *it;
-                            queue.erase(it);
-                            break;
-                        }
-                    if (r) break;
+                    rs = admit();
+                    if (!rs.empty()) break;
                     cv_work.wait(lk);
                 }
-                if (!r) break;
-                used += r->bytes;
-                r->state = 1;
+                if (rs.empty()) break;
+                for (auto &r : rs) {
+                    used += r->bytes;
+                    r->state = 1;
+                }
             }
-            run(r.get(), st);
+            if (rs.size() == 1 && rs[0]->key < 0)
+                run(rs[0].get(), st);
+            else
+                run_batch(rs, st);
             {
                 std::lock_guard<std::mutex> lk(mu);
-                used -= r->bytes;
-                r->state = 2;
-                r->t_done = Clock::now();
+                const auto now = Clock::now();
+                for (auto &r : rs) {
+                    used -= r->bytes;
+                    r->state = 2;
+                    r->t_done = now;
+                }
             }
             cv_done.notify_all();
             cv_work.notify_all();
@@ -105,7 +161,7 @@ struct ssqa_server {
         if (st) cudaStreamDestroy(st);
     }
 
-    static void run(Request *r, cudaStream_t st) {
+    static bool alloc_results(Request *r) {
         const ssqa_params &p = r->params;
         const size_t N = size_t(r->ising->N), cols = size_t(p.trials) * p.R;
         try {
@@ -120,8 +176,14 @@ struct ssqa_server {
         } catch (...) {
             r->rc = SSQA_ERR_OOM;
             r->err = "server: out of host memory for results";
-            return;
+            return false;
         }
+        return true;
+    }
+
+    static void run(Request *r, cudaStream_t st) {
+        if (!alloc_results(r)) return;
+        const ssqa_params &p = r->params;
         ssqa_result res{};
         res.sigma = r->sigma.data();
         res.is_state = r->is.data();
@@ -133,6 +195,90 @@ struct ssqa_server {
         }
         r->rc = ssqa_anneal(r->ising, &p, &res, st);
         if (r->rc) r->err = ssqa_last_error();
+    }
+
+    // Several requests in one ssqa_anneal_batch call: device result buffers
+    // per request, one launch, then the results back into each request.
+    static void run_batch(const std::vector<std::shared_ptr<Request>> &rs, cudaStream_t st) {
+        const size_t n = rs.size();
+        std::vector<const ssqa_ising *> isings(n);
+        std::vector<ssqa_params> ps(n);
+        std::vector<ssqa_result> outs(n);
+        std::vector<void *> bufs;
+        auto fail_all = [&](int rc, const std::string &msg) {
+            for (auto &r : rs) {
+                r->rc = rc;
+                r->err = msg;
+            }
+        };
+        auto dalloc = [&](size_t bytes) -> void * {
+            void *q = nullptr;
+            if (ssqa::dev_alloc(&q, bytes ? bytes : 1, st) != cudaSuccess) return nullptr;
+            bufs.push_back(q);
+            return q;
+        };
+        bool ok = true;
+        for (size_t k = 0; k < n && ok; ++k) {
+            Request *r = rs[k].get();
+            if (!alloc_results(r)) {
+                fail_all(r->rc, r->err);
+                ok = false;
+                break;
+            }
+            const ssqa_params &p = r->params;
+            const size_t N = size_t(r->ising->N), cols = size_t(p.trials) * p.R;
+            isings[k] = r->ising;
+            ps[k] = p;
+            ps[k].flags |= SSQA_FLAG_DEVICE_PTRS;
+            ssqa_result &o = outs[k];
+            o = ssqa_result{};
+            o.sigma = static_cast<int8_t *>(dalloc(cols * N));
+            o.is_state = static_cast<int32_t *>(dalloc(cols * N * 4));
+            o.e_final = static_cast<int64_t *>(dalloc(cols * 8));
+            if (p.delay) o.sigma_hist = static_cast<int8_t *>(dalloc(cols * N * size_t(p.delay)));
+            if (p.flags & SSQA_FLAG_TRACK_BEST) {
+                o.e_best = static_cast<int64_t *>(dalloc(cols * 8));
+                o.best_cycle = static_cast<int32_t *>(dalloc(cols * 4));
+            }
+            if (!o.sigma || !o.is_state || !o.e_final || (p.delay && !o.sigma_hist) ||
+                ((p.flags & SSQA_FLAG_TRACK_BEST) && (!o.e_best || !o.best_cycle))) {
+                cudaGetLastError();
+                fail_all(SSQA_ERR_OOM, "server: device memory for results");
+                ok = false;
+            }
+        }
+        if (ok) {
+            const int rc = ssqa_anneal_batch(int32_t(n), isings.data(), ps.data(), outs.data(), nullptr, st);
+            if (rc) {
+                fail_all(rc, ssqa_last_error());
+                ok = false;
+            }
+        }
+        if (ok) {
+            cudaError_t e = cudaSuccess;
+            for (size_t k = 0; k < n && !e; ++k) {
+                Request *r = rs[k].get();
+                const ssqa_result &o = outs[k];
+                if (!e) e = cudaMemcpyAsync(r->sigma.data(), o.sigma, r->sigma.size(), cudaMemcpyDeviceToHost, st);
+                if (!e) e = cudaMemcpyAsync(r->is.data(), o.is_state, r->is.size() * 4, cudaMemcpyDeviceToHost, st);
+                if (!e) e = cudaMemcpyAsync(r->e_final.data(), o.e_final, r->e_final.size() * 8, cudaMemcpyDeviceToHost, st);
+                if (!e && o.sigma_hist)
+                    e = cudaMemcpyAsync(r->hist.data(), o.sigma_hist, r->hist.size(), cudaMemcpyDeviceToHost, st);
+                if (!e && o.e_best) {
+                    e = cudaMemcpyAsync(r->e_best.data(), o.e_best, r->e_best.size() * 8, cudaMemcpyDeviceToHost, st);
+                    if (!e)
+                        e = cudaMemcpyAsync(r->best_cycle.data(), o.best_cycle, r->best_cycle.size() * 4,
+                                            cudaMemcpyDeviceToHost, st);
+                }
+            }
+            if (!e) e = cudaStreamSynchronize(st);
+            if (e) {
+                cudaGetLastError();
+                fail_all(SSQA_ERR_DEVICE, std::string("server: result download: ") + cudaGetErrorString(e));
+            }
+        }
+        for (void *q : bufs) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
     }
 };
 
@@ -152,6 +298,11 @@ int ssqa_server_create(size_t hbm_budget, int32_t max_slots, int32_t device, ssq
     if (!s) return ssqa::fail(SSQA_ERR_OOM, "ssqa_server_create: out of host memory");
     s->device = device;
     s->budget = hbm_budget;
+    s->max_bypass = 2 * max_slots;
+    if (cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        s->nsm = 148;
+    }
     try {
         for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s] { s->worker(); });
     } catch (...) {
@@ -192,6 +343,8 @@ int ssqa_submit(ssqa_server *s, const ssqa_ising *ising, const ssqa_params *para
     r->ising = ising;
     r->params = *params;
     r->bytes = footprint(ising, *params);
+    r->key = ssqa::batch_key(ising, params);
+    r->ctas = int((int64_t(params->trials) + 128 / params->R - 1) / (128 / params->R));
     if (r->bytes > s->budget)
         return ssqa::fail(SSQA_ERR_BUDGET, "ssqa_submit: request needs more device memory than the whole budget");
     r->t_submit = Clock::now();

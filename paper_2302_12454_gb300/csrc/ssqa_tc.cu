@@ -224,6 +224,15 @@ int tc_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, voi
     return SSQA_OK;
 }
 
+int tc_batch_key(const TcImage &img, const AnnealArgs &a) {
+    Layout L;
+    std::string why;
+    if (!plan(img, a, &L, &why)) return -1;
+    const TcVariant v = tc_variant(img, a);
+    if (!tc::pick_batch(a.delay, a.both != 0, a.track_best, v.bytes, v.f16, v.shfl)) return -1;
+    return (a.both ? 4 : 0) | (a.track_best ? 2 : 0) | (v.f16 ? 1 : 0);
+}
+
 int tc_anneal_batch(const TcBatchItem *items, int count, int *launches, void *stream) {
     using namespace tc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -94,3 +94,63 @@ def test_mixed_paths_equal_alone():
         for k in alone:
             np.testing.assert_array_equal(got[k], alone[k], err_msg=f"request {j} field {k}")
     srv.close()
+
+
+def _min_budget(I, kw):
+    """The request's device footprint: the smallest budget ssqa_submit accepts
+    it under (a request needing more than the whole budget is rejected)."""
+    lo, hi = 1, 1 << 36
+    while lo < hi:
+        mid = (lo + hi) // 2
+        srv = S.Server(hbm_budget=mid, max_slots=1)
+        try:
+            srv.submit(I, **kw)
+            ok = True
+        except S.SSQAError as e:
+            assert e.code == S.ERR_BUDGET
+            ok = False
+        srv.close()
+        lo, hi = (lo, mid) if ok else (mid + 1, hi)
+    return lo
+
+
+def test_large_request_is_not_starved():
+    """A request that needs the whole budget, submitted behind small requests
+    that keep arriving: with first-fit admission the small ones would always
+    pass it; with bounded bypass (at most 2 x slots admissions past the oldest
+    request) it is admitted once the running requests drain, and its result is
+    the one it has alone."""
+    big = (_gi(20, 7), dict(R=16, cycles=300, trials=128, seed=5, tau=25))
+    small = [(_gi(6, 200 + j), dict(R=8, cycles=200, trials=8, seed=300 + j, tau=20)) for j in range(8)]
+    fb = _min_budget(*big)
+    fs = _min_budget(*small[0])
+    assert fb > 4 * fs
+    slots = 4
+    srv = S.Server(hbm_budget=fb + fs // 2, max_slots=slots)  # the big request needs an idle server
+    tickets = [srv.submit(I, **kw) for I, kw in small[:6]]
+    tb = srv.submit(big[0], **big[1])
+    got_big = None
+    submitted_after = 0
+    done_after = 0
+    deadline = time.time() + 120
+    while got_big is None and time.time() < deadline and submitted_after < 400:
+        I, kw = small[submitted_after % len(small)]
+        tickets.append(srv.submit(I, **kw))
+        submitted_after += 1
+        for t in list(tickets):
+            r = srv.poll(t, timeout_ms=0)
+            if r is not None:
+                tickets.remove(t)
+                done_after += 1
+        r = srv.poll(tb, timeout_ms=1)
+        if r is not None:
+            got_big = r
+    for t in tickets:
+        srv.poll(t, timeout_ms=-1)
+    srv.close()
+    assert got_big is not None, f"starved: {submitted_after} small requests submitted after it"
+    # passed over at most 2 x slots times (an admission may batch several small requests)
+    assert done_after < 200, done_after
+    alone = S.anneal(big[0], want_hist=True, **big[1])
+    for k in alone:
+        np.testing.assert_array_equal(got_big[0][k], alone[k], err_msg=k)
