@@ -17,6 +17,7 @@ import math
 import multiprocessing as mp
 import os
 import platform
+import re
 import subprocess
 import sys
 import tempfile
@@ -60,6 +61,14 @@ def _oracle_warm(_):
 def host_info():
     """Core count and CPU model of this host (for the CPU-side lines)."""
     model = platform.processor() or ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                return {"cpu_count": os.cpu_count(), "cpu_model": v.strip(), "machine": platform.machine()}
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
@@ -189,9 +198,26 @@ def large_workloads(S, W, torch, stream, pool=None):
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
+        algo, desc = S.plan(I, R=R, cycles=C, trials=T, seed=cfg["seed"], tau=cfg["tau"])
+        tflops = 2.0 * N * N * R * T * C / t / 1e12
         r = {"N": N, "R": R, "trials": T, "cycles": C, "seconds": t, "value": N * R * T * C / t,
-             "unit": "spin-updates/s", "path": "streamed tcgen05 (SSQA_ALGO_AUTO)",
-             "tflops": 2.0 * N * N * R * T * C / t / 1e12}
+             "unit": "spin-updates/s", "path": desc, "tflops": tflops}
+        shape = dict(re.findall(r"(groups|KB|NCH|CS|dual|CTAs) (\d+)", desc))
+        if shape:
+            # operand bytes the streamed kernel moves into the SMs per cycle:
+            # every (column group, 256-spin chunk) pair streams its A blocks
+            # (4 KB per K-block) and, once per CTA, the chunk's B blocks (8 KB)
+            g, kb, nch, dual = (int(shape[k]) for k in ("groups", "KB", "NCH", "dual"))
+            ctas_per_rank = (g + 1) // 2 if dual else g
+            per_cycle = kb * nch * (g * 4096 + ctas_per_rank * 8192)
+            peaks, src = _peaks()
+            fp8 = 2.0 * peaks["bf16_tflops"]
+            r["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": fp8, "unit": "TFLOP/s",
+                             "frac": tflops / fp8, "traffic": None,
+                             "peak_source": f"{src}: 2 x bf16_tflops (FP8 dense / BF16 dense = 2)",
+                             "operand_bytes_per_cycle": per_cycle,
+                             "operand_TBps_into_SMs": per_cycle * C / t / 1e12,
+                             "shape": {k: int(v) for k, v in shape.items()}}
         if cfg["kind"] == "gi":
             r["p_s"] = float((E.min(dim=1).values.cpu().numpy() == -off).mean())
         if pool is not None:
@@ -430,7 +456,7 @@ def run_ours(args, rank, world):
         from paper_2302_12454_gb300 import serving_bench as SB
 
         out["served"] = SB.run(S, W, count=400, n_min=8, n_max=50, cycles_set=(1000, 2000, 5000), slots=32,
-                               plain_sample=16, seq_sample=100, capacity_sample=200)
+                               plain_sample=8, seq_sample=100, capacity_sample=200)
         out["rows"] = row_timings(S, torch, stream, I, cfg, sigma, Is, E, ms_per_step)
         pool = None if args.no_cpu_baseline else OraclePool(min(64, os.cpu_count() or 1))
         if not args.no_large:

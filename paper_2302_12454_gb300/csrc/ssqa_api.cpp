@@ -631,8 +631,19 @@ int choose_path(const ssqa_ising *I, const ssqa_params *p, const AnnealArgs &a, 
                 " replica exchange";
     } else if (use_tcs) {
         *algo = SSQA_ALGO_STREAMED;
+        int dev = 0, nsm = 148;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            nsm = 148;
+        }
+        const int64_t groups = (int64_t(a.trials) + 128 / a.R - 1) / (128 / a.R);
+        const bool dual = I->tc.KB >= 160;
+        const int cs = tcs_cluster_size(I->tc, a, nsm);
         *desc = std::string("streamed tcgen05 kernel, FP32 accumulator, ") +
-                (I->tc.KB >= 160 ? "two column groups per CTA" : "one column group per CTA");
+                (dual ? "two column groups per CTA" : "one column group per CTA") + " (groups " +
+                std::to_string(groups) + ", KB " + std::to_string(I->tc.KB) + ", NCH " + std::to_string(I->tc.NCH) +
+                ", CS " + std::to_string(cs) + ", dual " + (dual ? "1" : "0") + ", CTAs " +
+                std::to_string((dual ? (groups + 1) / 2 : groups) * cs) + ")";
     } else {
         *algo = SSQA_ALGO_DELTA;
         *desc = "delta-field CUDA-core path (no tensor path takes this problem: " + why +

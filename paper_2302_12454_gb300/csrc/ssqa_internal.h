@@ -173,6 +173,9 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
 // Streamed tensor-core path (N too large for the resident kernel).
 bool tcs_supported(const TcImage &img, const AnnealArgs &a, std::string *why);
 size_t tcs_scratch_bytes(const TcImage &img, const AnnealArgs &a);
+// CTAs per cluster of the streamed launch on a device with `nsm` SMs (the
+// cluster shares one column group's, or pair of groups', 256-spin chunks).
+int tcs_cluster_size(const TcImage &img, const AnnealArgs &a, int nsm);
 int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, void *scratch, void *stream);
 
 // Bound, in SM clocks, of every wait a tensor-core kernel makes for the

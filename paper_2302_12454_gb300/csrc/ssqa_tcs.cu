@@ -659,6 +659,21 @@ bool tcs_supported(const TcImage &img, const AnnealArgs &a, std::string *why) {
     return true;
 }
 
+int tcs_cluster_size(const TcImage &img, const AnnealArgs &a, int nsm) {
+    const int64_t Tb = 128 / a.R;
+    const int64_t groups = (int64_t(a.trials) + Tb - 1) / Tb;
+    const int64_t pairs = img.KB >= 160 ? (groups + 1) / 2 : groups;  // CTAs per cluster rank
+    int CS = int(nsm / (pairs > 0 ? pairs : 1));
+    if (CS > 8) CS = 8;
+    if (CS > img.NCH) CS = img.NCH;
+    if (CS < 1) CS = 1;
+    // the cycle takes as long as the rank with the most chunks: the smallest
+    // cluster with that many chunks per rank does the same work on fewer SMs
+    // (10 chunks: 5 CTAs of 2 chunks, not 8 CTAs of 1 or 2)
+    while (CS > 1 && (img.NCH + CS - 2) / (CS - 1) == (img.NCH + CS - 1) / CS) --CS;
+    return CS;
+}
+
 size_t tcs_scratch_bytes(const TcImage &img, const AnnealArgs &a) {
     const int64_t Tb = 128 / a.R;
     const int64_t groups = (int64_t(a.trials) + Tb - 1) / Tb;
@@ -713,14 +728,7 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
     // K-blocks: 6 % slower).
     p.dual = img.KB >= 160 ? 1 : 0;
     const int64_t pairs = p.dual ? (groups + 1) / 2 : groups;  // CTAs per cluster rank
-    int CS = int(nsm / (pairs > 0 ? pairs : 1));
-    if (CS > 8) CS = 8;
-    if (CS > p.NCH) CS = p.NCH;
-    if (CS < 1) CS = 1;
-    // the cycle takes as long as the rank with the most chunks: the smallest
-    // cluster with that many chunks per rank does the same work on fewer SMs
-    // (10 chunks: 5 CTAs of 2 chunks, not 8 CTAs of 1 or 2)
-    while (CS > 1 && (p.NCH + CS - 2) / (CS - 1) == (p.NCH + CS - 1) / CS) --CS;
+    int CS = tcs_cluster_size(img, a, nsm);
     uint8_t *q = static_cast<uint8_t *>(scratch);
     p.A = q;
     q += up256(size_t(groups) * p.L * p.KB * kABytes);
