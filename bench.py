@@ -168,13 +168,13 @@ class ClockSampler:
 
 # -------------------------------------------------------------- our arm
 def large_workloads(S, W, torch, stream, pool=None):
-    """The two large configurations (one anneal each, default path = the
-    streamed tensor kernel), timed with CUDA events after a warm-up call that
-    uploads the instance.  Informational: the headline is the batched N = 400
+    """The large configurations (GI n = 50 at p = 0.5, 0.3 and 0.7, SK N =
+    8192; one anneal each, default path = the streamed tensor kernel), timed
+    with CUDA events after a warm-up call that uploads the instance.  Informational: the headline is the batched N = 400
     workload.  With `cores`, also the oracle's rate on a bounded sample of the
     same instance (one trial per core, a few cycles), per spin update."""
     res = {}
-    for name in ("large_gi_n50", "sk_n8192"):
+    for name in ("large_gi_n50", "large_gi_n50_p03", "large_gi_n50_p07", "sk_n8192"):
         cfg = dict(W.CONFIGS[name])
         if cfg["kind"] == "gi":
             a = S.gen_er_graph(cfg["n"], W.p_q32(cfg["p"]), cfg["graph_seed"])

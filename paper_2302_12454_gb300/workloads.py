@@ -21,6 +21,11 @@ CONFIGS = {
                            trials=1024, tau=100),
     "large_gi_n50": dict(kind="gi", n=50, p=0.5, graph_seed=21, perm_seed=22, seed=23, R=32, cycles=5000,
                          trials=256, tau=100),
+    # the same size at the other two edge densities of the large GI workload
+    "large_gi_n50_p03": dict(kind="gi", n=50, p=0.3, graph_seed=24, perm_seed=25, seed=26, R=32, cycles=5000,
+                             trials=256, tau=100),
+    "large_gi_n50_p07": dict(kind="gi", n=50, p=0.7, graph_seed=27, perm_seed=28, seed=29, R=32, cycles=5000,
+                             trials=256, tau=100),
     "sk_n8192": dict(kind="sk", N=8192, j_seed=31, seed=33, R=32, cycles=2000, trials=64, tau=100),
 }
 

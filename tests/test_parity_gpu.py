@@ -196,7 +196,7 @@ def test_batched_gi_n20_full_size_sampled_trials():
 
 
 # ----------------------------------- large instances: one-cycle transitions
-@pytest.mark.parametrize("kind", ["large_gi_n50", "sk_n8192"])
+@pytest.mark.parametrize("kind", ["large_gi_n50", "large_gi_n50_p03", "large_gi_n50_p07", "sk_n8192"])
 def test_large_instances_transition_sampled(kind):
     c = W.CONFIGS[kind]
     if c["kind"] == "gi":
