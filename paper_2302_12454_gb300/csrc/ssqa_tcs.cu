@@ -15,11 +15,11 @@
 //                  contiguous in both images), completing on mbarriers;
 //   MMA warp       issues per K-block one tcgen05.mma kind::f8f6f4 (M 128,
 //                  N <= 256, K 32) per group, all groups on the same B block;
-//   8 epilogue warps turn finished accumulators into sigma(t+1) of the chunk
-//                  (Eq. 6a-6c, the same packed-half2 arithmetic as the resident
-//                  kernel): in single mode while the next chunk's MMAs run
-//                  into the other of two TMEM buffers, in dual mode (one
-//                  buffer per group) before them;
+//   epilogue warps (8; 16 in dual mode) turn finished accumulators into
+//                  sigma(t+1) of the chunk (Eq. 6a-6c, the same packed-half2
+//                  arithmetic as the resident kernel): in single mode while
+//                  the next chunk's MMAs run into the other of two TMEM
+//                  buffers, in dual mode (one buffer per group) before them;
 // and a cluster barrier closes the cycle.  sigma lives in L2 as FP8 operand
 // blocks, one slot per history level (the replica term reads the ring
 // neighbour's sigma(t - d) from its slot), and the counters as bytes Is + 128.
@@ -55,8 +55,13 @@ constexpr int kBBytes = 256 * 32;   // one K-block of a B chunk
 constexpr int kStageBytes = kKps * (2 * kABytes + kBBytes);  // dual mode: A of both column groups, one B run
 constexpr int kStageBytes1 = kKps * (kABytes + kBBytes);     // single mode
 constexpr int kStagesDual = 3, kStagesSingle = 4;
-constexpr int kEpi = 8;             // epilogue warps (2 per TMEM lane quadrant)
-constexpr int kThr = (2 + kEpi) * 32;
+// Epilogue warps: 8 (2 per TMEM lane quadrant) in single mode, where a
+// chunk's epilogue hides under the next chunk's MMAs and 168 registers a
+// thread leave the prefetched loads unspilled; 16 (4 per quadrant) in dual
+// mode, where the MMAs wait for the epilogue (SK N = 8192: 0.357 s instead of
+// 0.39 s per anneal; 18 warps on four schedulers allow 96 registers).
+template <bool kDual> __host__ __device__ constexpr int epi_warps() { return kDual ? 16 : 8; }
+template <bool kDual> __host__ __device__ constexpr int cta_threads() { return (2 + epi_warps<kDual>()) * 32; }
 
 struct SParams {
     AnnealArgs a;
@@ -107,7 +112,10 @@ __device__ __forceinline__ int64_t slot_of(int64_t t, int32_t L) { return ((t % 
 
 // ------------------------------------------------------------------- kernel
 template <bool kTrack, bool kDual>
-__global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant__ SParams p) {
+__global__ void __launch_bounds__(cta_threads<kDual>(), 1) ssqa_tcs_kernel(const __grid_constant__ SParams p) {
+    constexpr int kEpi = epi_warps<kDual>();
+    constexpr int kParts = kEpi / 4;    // epilogue warps per TMEM lane quadrant
+    constexpr int kPairs = 4 / kParts;  // word pairs (w, w + 4) of a chunk per thread
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *ring = sm;
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
     uint32_t et_ph = 0u;   // epilogue: tmem-full parity per buffer (bit b)
 
     // epilogue identity: TMEM lane quadrant qd (column c of each group), part
-    // 0 / 1 of the words; accumulators at TMEM column 256 gi (dual mode,
+    // 0 .. kParts - 1 of the words; accumulators at TMEM column 256 gi (dual mode,
     // group gi) or 256 (m & 1) (single mode, the CTA's m-th chunk)
     const int ew = warp - 2;
     const int qd = warp & 3, part = ew >> 2;
@@ -312,28 +320,31 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                 const uint8_t *Aold = Ag + old_off;
                 uint8_t *Anext = Ag + next_off;
                 long long esum = 0;
-                // This thread's words of the chunk: 8 ch + 2 part + {0, 4, 1, 5}.
-                // Words 8 ch + 2 part and + 4 share one Philox call (same counter),
-                // as do + 1 and + 5; both calls are made before the MMAs are awaited.
-                // Output word of word w is (w / 4) % 4 = (2 ch + (q & 1)) % 4.
-                const int wbase = 8 * ch + 2 * part;
-                uint32_t nq0 = 0, nq1 = 0, nq2 = 0, nq3 = 0;
+                // This thread's words of the chunk: the kPairs pairs (w, w + 4), w =
+                // 8 ch + kPairs part + j.  The words of a pair share one Philox call (same
+                // counter), made before the MMAs are awaited; the output of word w is
+                // (w / 4) % 4 = 2 (ch % 2) for w and 2 (ch % 2) + 1 for w + 4.
+                const int wbase = 8 * ch + kPairs * part;
+                uint32_t nq[2 * kPairs];
+#pragma unroll
+                for (int j = 0; j < 2 * kPairs; ++j) nq[j] = 0;
                 if (update) {
-                    const Philox4 ph0 = philox4x32_10(noise_ctr(uint32_t(wbase)), uint32_t(k), trial_g, uint32_t(t),
-                                                      uint32_t(a.seed), uint32_t(a.seed >> 32));
-                    const Philox4 ph1 = philox4x32_10(noise_ctr(uint32_t(wbase + 1)), uint32_t(k), trial_g,
-                                                      uint32_t(t), uint32_t(a.seed), uint32_t(a.seed >> 32));
                     const bool odd = ch & 1;
-                    nq0 = odd ? ph0.x[2] : ph0.x[0];
-                    nq1 = odd ? ph0.x[3] : ph0.x[1];
-                    nq2 = odd ? ph1.x[2] : ph1.x[0];
-                    nq3 = odd ? ph1.x[3] : ph1.x[1];
+#pragma unroll
+                    for (int j = 0; j < kPairs; ++j) {
+                        const Philox4 ph = philox4x32_10(noise_ctr(uint32_t(wbase + j)), uint32_t(k), trial_g,
+                                                         uint32_t(t), uint32_t(a.seed), uint32_t(a.seed >> 32));
+                        nq[2 * j] = odd ? ph.x[2] : ph.x[0];
+                        nq[2 * j + 1] = odd ? ph.x[3] : ph.x[1];
+                    }
                 }
                 // Granule g of the chunk (q = g / 2, hh = g % 2): spins i0 .. i0 + 15 of
-                // word wbase + 4 (q % 2) + q / 2.  Its counters and its upper ring
-                // neighbour's sigma(t - d) do not depend on this cycle's MMAs; in single
-                // mode all eight granules' values are loaded before the accumulator is
-                // awaited, so that their L2 latencies overlap the wait and each other.
+                // word wbase + q / 2 + 4 (q % 2), noise word nq[q].  Its counters and its
+                // upper ring neighbour's sigma(t - d) do not depend on this cycle's MMAs;
+                // in single mode all the thread's granules' values are loaded before the
+                // accumulator is awaited, so that their L2 latencies overlap the wait and
+                // each other.
+                constexpr int kGran = 4 * kPairs;
                 auto gran_i0 = [&](int g) { return 32 * (wbase + 4 * ((g >> 1) & 1) + (g >> 2)) + 16 * (g & 1); };
                 auto is_ptr = [&](int i0) { return p.IsB + (int64_t(i0 >> 4) * cols + gcol) * 16; };
                 auto nu_ptr = [&](int i0) { return Aold + int64_t(i0 >> 5) * kABytes + blk_off(nb_up, i0 & 31); };
@@ -347,10 +358,10 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                         nu = isv;
                     }
                 };
-                uint4 pis[kDual ? 1 : 8], pnu[kDual ? 1 : 8];
+                uint4 pis[kDual ? 1 : kGran], pnu[kDual ? 1 : kGran];
                 if constexpr (!kDual) {
 #pragma unroll
-                    for (int g = 0; g < 8; ++g) gran_loads(g, pis[g], pnu[g]);
+                    for (int g = 0; g < kGran; ++g) gran_loads(g, pis[g], pnu[g]);
                 }
                 if (gi == 0) {  // the chunk's accumulators (of both groups)
                     const bool ok = mbar_wait(&tfull[b], (et_ph >> b) & 1u, p.wait_clocks);
@@ -366,7 +377,10 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                     const int q = g >> 1, hh = g & 1;
                     const int i0 = gran_i0(g);
                     if (i0 >= p.N16) return;  // warp-uniform
-                    const uint32_t nw = q == 0 ? nq0 : (q == 1 ? nq1 : (q == 2 ? nq2 : nq3));
+                    uint32_t nw = nq[0];  // nq[q] by selects (g is a loop variable in dual mode)
+#pragma unroll
+                    for (int j = 1; j < 2 * kPairs; ++j)
+                        if (q == j) nw = nq[j];
                     uint32_t f[16];
                     __syncwarp();
                     tmem_ld16_issue(tmem + (uint32_t(qd * 32) << 16) + uint32_t((b + gi) * 256 + (i0 - 256 * ch)), f);
@@ -436,10 +450,10 @@ __global__ void __launch_bounds__(kThr, 1) ssqa_tcs_kernel(const __grid_constant
                 };
                 if constexpr (!kDual) {
 #pragma unroll
-                    for (int g = 0; g < 8; ++g) granule(g, pis[g], pnu[g]);
+                    for (int g = 0; g < kGran; ++g) granule(g, pis[g], pnu[g]);
                 } else {
 #pragma unroll 1
-                    for (int g = 0; g < 8; ++g) {
+                    for (int g = 0; g < kGran; ++g) {
                         uint4 isv, nu;
                         gran_loads(g, isv, nu);
                         granule(g, isv, nu);
@@ -758,11 +772,12 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
     }
     void (*fn)(SParams) = a.track_best ? (p.dual ? ssqa_tcs_kernel<true, true> : ssqa_tcs_kernel<true, false>)
                                        : (p.dual ? ssqa_tcs_kernel<false, true> : ssqa_tcs_kernel<false, false>);
+    const int threads = p.dual ? cta_threads<true>() : cta_threads<false>();
     const int smem = p.dual ? kStagesDual * kStageBytes + 1024 + 512   // ring + alignment + barriers
                             : kStagesSingle * kStageBytes1 + 1024 + 512;
     configure_once(fn, smem);
     cudaLaunchConfig_t cfg{};
-    cfg.blockDim = dim3(kThr, 1, 1);
+    cfg.blockDim = dim3(unsigned(threads), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
