@@ -34,9 +34,11 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <set>
 #include <string>
+#include <tuple>
 #include <utility>
 
 #include "ssqa_tc_kernel.cuh"
@@ -673,19 +675,81 @@ bool tcs_supported(const TcImage &img, const AnnealArgs &a, std::string *why) {
     return true;
 }
 
+namespace {
+struct LaunchCfg {
+    void (*fn)(tcs::SParams);
+    int threads, smem;
+};
+LaunchCfg launch_cfg(bool dual, bool track) {
+    using namespace tcs;
+    LaunchCfg c;
+    c.fn = track ? (dual ? ssqa_tcs_kernel<true, true> : ssqa_tcs_kernel<true, false>)
+                 : (dual ? ssqa_tcs_kernel<false, true> : ssqa_tcs_kernel<false, false>);
+    c.threads = dual ? cta_threads<true>() : cta_threads<false>();
+    c.smem = (dual ? kStagesDual * kStageBytes : kStagesSingle * kStageBytes1) + 1024 + 512;  // ring, alignment, barriers
+    return c;
+}
+}  // namespace
+
 int tcs_cluster_size(const TcImage &img, const AnnealArgs &a, int nsm) {
     const int64_t Tb = 128 / a.R;
     const int64_t groups = (int64_t(a.trials) + Tb - 1) / Tb;
-    const int64_t pairs = img.KB >= 160 ? (groups + 1) / 2 : groups;  // CTAs per cluster rank
-    int CS = int(nsm / (pairs > 0 ? pairs : 1));
-    if (CS > 8) CS = 8;
-    if (CS > img.NCH) CS = img.NCH;
-    if (CS < 1) CS = 1;
-    // the cycle takes as long as the rank with the most chunks: the smallest
-    // cluster with that many chunks per rank does the same work on fewer SMs
-    // (10 chunks: 5 CTAs of 2 chunks, not 8 CTAs of 1 or 2)
-    while (CS > 1 && (img.NCH + CS - 2) / (CS - 1) == (img.NCH + CS - 1) / CS) --CS;
-    return CS;
+    const bool dual = img.KB >= 160;
+    const int64_t clusters = dual ? (groups + 1) / 2 : groups;  // one per column group (pair), CTAs per chunk rank
+    // A cycle takes as long as the rank with the most chunks.  Take the
+    // smallest cluster that reaches the fewest chunks per rank among those
+    // whose clusters all fit on the device at once, up to 16 CTAs (a
+    // non-portable size): SK N = 8192 runs 8 clusters of 11 ranks with at most
+    // 3 chunks each in 0.27 s, against 8 ranks of 4 chunks in 0.35 s; 16 ranks
+    // of 2 do not all fit.  N = 2500: 2 ranks of 5 chunks (3 would need 192 SMs).
+    // Without a device, portable sizes (<= 8) are assumed to fit.
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    const LaunchCfg lc = launch_cfg(dual, a.track_best);
+    static std::mutex mu;
+    static std::map<std::tuple<int, void (*)(tcs::SParams), int64_t, int, int>, int> memo;
+    const auto key = std::make_tuple(dev, lc.fn, clusters, img.NCH, nsm);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+    }
+    if (dev >= 0) tcs::configure_once(lc.fn, lc.smem);
+    int best = 1, best_chunks = img.NCH;
+    for (int cs = 2; cs <= 16 && cs <= img.NCH; ++cs) {
+        const int chunks = (img.NCH + cs - 1) / cs;
+        if (chunks >= best_chunks) continue;
+        if (clusters * cs > nsm) break;
+        if (dev >= 0) {
+            cudaLaunchConfig_t cfg{};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = unsigned(cs);
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(unsigned(clusters * cs), 1, 1);
+            cfg.blockDim = dim3(unsigned(lc.threads), 1, 1);
+            cfg.dynamicSmemBytes = size_t(lc.smem);
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclus = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclus, lc.fn, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (nclus < clusters) continue;
+        } else if (cs > 8) {
+            break;
+        }
+        best = cs;
+        best_chunks = chunks;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    memo[key] = best;
+    return best;
 }
 
 size_t tcs_scratch_bytes(const TcImage &img, const AnnealArgs &a) {
@@ -770,11 +834,9 @@ int tcs_anneal(const TcImage &img, const DeviceCopy &dc, const AnnealArgs &a, vo
             return fail(SSQA_ERR_UNSUPPORTED, "streamed tensor path: resumed counters outside -128..127");
         }
     }
-    void (*fn)(SParams) = a.track_best ? (p.dual ? ssqa_tcs_kernel<true, true> : ssqa_tcs_kernel<true, false>)
-                                       : (p.dual ? ssqa_tcs_kernel<false, true> : ssqa_tcs_kernel<false, false>);
-    const int threads = p.dual ? cta_threads<true>() : cta_threads<false>();
-    const int smem = p.dual ? kStagesDual * kStageBytes + 1024 + 512   // ring + alignment + barriers
-                            : kStagesSingle * kStageBytes1 + 1024 + 512;
+    const LaunchCfg lc = launch_cfg(p.dual != 0, a.track_best);
+    void (*fn)(SParams) = lc.fn;
+    const int threads = lc.threads, smem = lc.smem;
     configure_once(fn, smem);
     cudaLaunchConfig_t cfg{};
     cfg.blockDim = dim3(unsigned(threads), 1, 1);
