@@ -2,6 +2,7 @@
 // (Sec. 4.1-4.2 of the paper), device copies, and dispatch of the anneal to
 // the CUDA kernels.  Every step of an anneal runs on the GPU.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -668,7 +669,19 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 }  // namespace
 
+namespace {
+// A named range on the calling thread's NVTX stack for the span of one entry
+// point (shown by profilers that record NVTX; a no-op without one).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace
+
 extern "C" int ssqa_anneal(const ssqa_ising *I, const ssqa_params *p, ssqa_result *r, void *stream) {
+    const Range range("ssqa_anneal");
     int rc = validate(I, p, r);
     if (rc) return rc;
     DeviceCopy *dc = nullptr;
@@ -795,6 +808,7 @@ int batch_key(const ssqa_ising *I, const ssqa_params *p) {
 
 extern "C" int ssqa_anneal_batch(int32_t count, const ssqa_ising *const *isings, const ssqa_params *params,
                                  ssqa_result *outs, int32_t *launches, void *stream) {
+    const Range range("ssqa_anneal_batch");
     if (launches) *launches = 0;
     if (count < 0 || (count > 0 && (!isings || !params || !outs)))
         return fail(SSQA_ERR_INVALID_ARG, "ssqa_anneal_batch: bad count or NULL array");
@@ -870,6 +884,7 @@ extern "C" int ssqa_plan(const ssqa_ising *I, const ssqa_params *p, char *desc, 
 
 extern "C" int ssqa_energy(const ssqa_ising *I, const int8_t *sigma, int64_t count, int64_t *E_out, uint32_t flags,
                            void *stream) {
+    const Range range("ssqa_energy");
     if (!I || !sigma || !E_out || count < 0) return fail(SSQA_ERR_INVALID_ARG, "ssqa_energy: bad arguments");
     if (flags & ~uint32_t(SSQA_FLAG_DEVICE_PTRS)) return fail(SSQA_ERR_INVALID_ARG, "ssqa_energy: unknown flags");
     if (count == 0) return SSQA_OK;
