@@ -12,6 +12,7 @@ collective on the data path).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import multiprocessing as mp
@@ -320,7 +321,9 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
+        # a rank that dies or never joins ends the others' next collective with an
+        # error after this bound instead of holding their GPUs
+        dist.init_process_group("nccl", timeout=datetime.timedelta(minutes=10))
     n, R, cycles, trials = cfg["n"], cfg["R"], cfg["cycles"], cfg["trials"]
     a = S.gen_er_graph(n, W.p_q32(cfg["p"]), cfg["graph_seed"])
     b, _ = S.permute_graph(a, cfg["perm_seed"])

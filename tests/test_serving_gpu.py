@@ -154,3 +154,29 @@ def test_large_request_is_not_starved():
     alone = S.anneal(big[0], want_hist=True, **big[1])
     for k in alone:
         np.testing.assert_array_equal(got_big[0][k], alone[k], err_msg=k)
+
+
+def test_failed_request_reports_its_error_and_the_server_recovers():
+    """A request whose anneal fails on the device (its bounded waits made to run
+    out with a 100-clock limit, the only failure injected) reports
+    SSQA_ERR_TIMEOUT on poll; the worker frees its budget and slot and the next
+    requests, with the default limit restored, give the results of the same
+    anneals run alone."""
+    srv = S.Server(hbm_budget=1 << 30, max_slots=2)
+    I = _gi(20, 7)
+    kw = dict(R=16, cycles=40, trials=64, seed=17, tau=10)
+    S.set_wait_limit(100)
+    try:
+        t = srv.submit(I, **kw)
+        with pytest.raises(S.SSQAError) as e:
+            srv.poll(t, timeout_ms=-1)
+        assert e.value.code == S.ERR_TIMEOUT, str(e.value)
+    finally:
+        S.set_wait_limit(0)
+    tickets = [srv.submit(I, **kw), srv.submit(_gi(9, 8), R=8, cycles=30, trials=5, seed=3)]
+    got = [srv.poll(t, timeout_ms=-1) for t in tickets]
+    for (out, _), (inst, kws) in zip(got, [(I, kw), (_gi(9, 8), dict(R=8, cycles=30, trials=5, seed=3))]):
+        alone = S.anneal(inst, want_hist=True, **kws)
+        for k in alone:
+            np.testing.assert_array_equal(out[k], alone[k], err_msg=k)
+    srv.close()
