@@ -68,8 +68,9 @@ extern "C" {
                               dense recompute when many flip); AUTO picks it when no
                               tensor path can take the instance                     */
 #define SSQA_ALGO_STREAMED 4 /* the streamed tcgen05 path only (N > 256): J streamed
-                              from L2 in 256-spin chunks, clusters of up to 8 CTAs
-                              per 128 spin columns; SSQA_ERR_UNSUPPORTED otherwise   */
+                              from L2 in 256-spin chunks, clusters of up to 16 CTAs
+                              per 128 (or 256) spin columns; SSQA_ERR_UNSUPPORTED
+                              otherwise                                              */
 
 #define SSQA_FLAG_TRACK_BEST 1u  /* fill e_best / best_cycle                      */
 #define SSQA_FLAG_DEVICE_PTRS 2u /* state / result pointers are device pointers  */
