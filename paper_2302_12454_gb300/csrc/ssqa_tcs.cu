@@ -10,7 +10,7 @@
 //   producer warp  streams, for each owned chunk, the K-blocks of A (sigma(t)
 //                  of 128 columns, 4 KB per group and K-block) and B (J rows
 //                  of the chunk, 8 KB per K-block) from L2 into a shared-memory
-//                  ring whose stages hold kKps consecutive K-blocks, one bulk
+//                  ring whose stages hold kps consecutive K-blocks, one bulk
 //                  async copy per operand and stage (consecutive K-blocks are
 //                  contiguous in both images), completing on mbarriers;
 //   MMA warp       issues per K-block one tcgen05.mma kind::f8f6f4 (M 128,
@@ -47,16 +47,21 @@ namespace ssqa {
 namespace tcs {
 using namespace tc;
 
-// A bulk copy's delivery rate into an SM follows the bytes it keeps in
-// flight: with about 192 KB outstanding an SM receives ~75 B/clk, with 12 KB
-// stages of one K-block it received ~23.  So a stage carries kKps K-blocks
-// (48 KB single, 64 KB dual) and the ring holds 4 (single) or 3 (dual) of them.
-constexpr int kKps = 4;             // K-blocks per ring stage
+// A bulk copy's delivery rate into an SM grows with the bytes it keeps in
+// flight (~75 B/clk with about 192 KB outstanding, ~23 with one 12 KB stage of
+// one K-block) and with the size of each copy: at N = 2500 (single mode) three
+// stages of 6 K-blocks (72 KB, one 24 KB and one 48 KB copy each) anneal in
+// 0.227 s, four of 4 K-blocks in 0.254 s, six of 3 in 0.286 s.  Dual mode keeps
+// three stages of 4 K-blocks (64 KB each; two stages of 6 took 0.311 s instead
+// of 0.268 s on SK N = 8192).
 constexpr int kABytes = 128 * 32;   // one K-block of A
 constexpr int kBBytes = 256 * 32;   // one K-block of a B chunk
-constexpr int kStageBytes = kKps * (2 * kABytes + kBBytes);  // dual mode: A of both column groups, one B run
-constexpr int kStageBytes1 = kKps * (kABytes + kBBytes);     // single mode
-constexpr int kStagesDual = 3, kStagesSingle = 4;
+template <bool kDual> __host__ __device__ constexpr int stage_kblocks() { return kDual ? 4 : 6; }
+template <bool kDual> __host__ __device__ constexpr int ring_stages() { return 3; }
+// dual mode: A of both column groups and one B run; single mode: A and B runs
+template <bool kDual> __host__ __device__ constexpr int stage_bytes() {
+    return stage_kblocks<kDual>() * ((kDual ? 2 : 1) * kABytes + kBBytes);
+}
 // Epilogue warps: 8 (2 per TMEM lane quadrant) in single mode, where a
 // chunk's epilogue hides under the next chunk's MMAs and 168 registers a
 // thread leave the prefetched loads unspilled; 16 (4 per quadrant) in dual
@@ -121,10 +126,11 @@ __global__ void __launch_bounds__(cta_threads<kDual>(), 1) ssqa_tcs_kernel(const
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *ring = sm;
-    // stage = A run of group 0 [kKps][128 x 32], (dual) A run of group 1, then
-    // the B run [kKps][256 x 32]
-    constexpr int kStages = kDual ? kStagesDual : kStagesSingle;
-    constexpr int sbytes = kDual ? kStageBytes : kStageBytes1;
+    // stage = A run of group 0 [kps][128 x 32], (dual) A run of group 1, then
+    // the B run [kps][256 x 32]
+    constexpr int kKps = stage_kblocks<kDual>();
+    constexpr int kStages = ring_stages<kDual>();
+    constexpr int sbytes = stage_bytes<kDual>();
     constexpr int a2off = kKps * kABytes;
     constexpr int boff = (kDual ? 2 : 1) * kKps * kABytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + kStages * sbytes);
@@ -686,7 +692,8 @@ LaunchCfg launch_cfg(bool dual, bool track) {
     c.fn = track ? (dual ? ssqa_tcs_kernel<true, true> : ssqa_tcs_kernel<true, false>)
                  : (dual ? ssqa_tcs_kernel<false, true> : ssqa_tcs_kernel<false, false>);
     c.threads = dual ? cta_threads<true>() : cta_threads<false>();
-    c.smem = (dual ? kStagesDual * kStageBytes : kStagesSingle * kStageBytes1) + 1024 + 512;  // ring, alignment, barriers
+    c.smem = (dual ? ring_stages<true>() * stage_bytes<true>() : ring_stages<false>() * stage_bytes<false>()) + 1024 +
+             512;  // ring, alignment, barriers
     return c;
 }
 }  // namespace
