@@ -57,7 +57,7 @@ using namespace tc;
 constexpr int kABytes = 128 * 32;   // one K-block of A
 constexpr int kBBytes = 256 * 32;   // one K-block of a B chunk
 template <bool kDual> __host__ __device__ constexpr int stage_kblocks() { return kDual ? 4 : 6; }
-template <bool kDual> __host__ __device__ constexpr int ring_stages() { return 3; }
+constexpr int kRingStages = 3;      // ring stages in both modes
 // dual mode: A of both column groups and one B run; single mode: A and B runs
 template <bool kDual> __host__ __device__ constexpr int stage_bytes() {
     return stage_kblocks<kDual>() * ((kDual ? 2 : 1) * kABytes + kBBytes);
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(cta_threads<kDual>(), 1) ssqa_tcs_kernel(const
     // stage = A run of group 0 [kps][128 x 32], (dual) A run of group 1, then
     // the B run [kps][256 x 32]
     constexpr int kKps = stage_kblocks<kDual>();
-    constexpr int kStages = ring_stages<kDual>();
+    constexpr int kStages = kRingStages;
     constexpr int sbytes = stage_bytes<kDual>();
     constexpr int a2off = kKps * kABytes;
     constexpr int boff = (kDual ? 2 : 1) * kKps * kABytes;
@@ -692,8 +692,7 @@ LaunchCfg launch_cfg(bool dual, bool track) {
     c.fn = track ? (dual ? ssqa_tcs_kernel<true, true> : ssqa_tcs_kernel<true, false>)
                  : (dual ? ssqa_tcs_kernel<false, true> : ssqa_tcs_kernel<false, false>);
     c.threads = dual ? cta_threads<true>() : cta_threads<false>();
-    c.smem = (dual ? ring_stages<true>() * stage_bytes<true>() : ring_stages<false>() * stage_bytes<false>()) + 1024 +
-             512;  // ring, alignment, barriers
+    c.smem = kRingStages * (dual ? stage_bytes<true>() : stage_bytes<false>()) + 1024 + 512;  // ring, alignment, barriers
     return c;
 }
 }  // namespace
