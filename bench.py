@@ -168,6 +168,20 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- our arm
+def streamed_shape(desc):
+    """The launch shape in a streamed-path plan description (`ssqa_plan`), and
+    the operand bytes that launch moves into the SMs per cycle: every (column
+    group, 256-spin chunk) pair streams its A blocks (4 KB per K-block) and each
+    CTA the chunk's B blocks (8 KB per K-block; two groups per CTA share them in
+    dual mode).  None for the other paths."""
+    shape = {k: int(v) for k, v in re.findall(r"(groups|KB|NCH|CS|dual|CTAs) (\d+)", desc)}
+    if not shape:
+        return None
+    g, kb, nch, dual = (shape[k] for k in ("groups", "KB", "NCH", "dual"))
+    ctas_per_rank = (g + 1) // 2 if dual else g
+    return shape, kb * nch * (g * 4096 + ctas_per_rank * 8192)
+
+
 def large_workloads(S, W, torch, stream, pool=None):
     """The large configurations (GI n = 50 at p = 0.5, 0.3 and 0.7, SK N =
     8192; one anneal each, default path = the streamed tensor kernel), timed
@@ -209,14 +223,9 @@ def large_workloads(S, W, torch, stream, pool=None):
         tflops = 2.0 * N * N * R * T * C / t / 1e12
         r = {"N": N, "R": R, "trials": T, "cycles": C, "seconds": t, "runs": ts, "value": N * R * T * C / t,
              "unit": "spin-updates/s", "path": desc, "tflops": tflops, "clocks": clk.summary()}
-        shape = dict(re.findall(r"(groups|KB|NCH|CS|dual|CTAs) (\d+)", desc))
-        if shape:
-            # operand bytes the streamed kernel moves into the SMs per cycle:
-            # every (column group, 256-spin chunk) pair streams its A blocks
-            # (4 KB per K-block) and, once per CTA, the chunk's B blocks (8 KB)
-            g, kb, nch, dual = (int(shape[k]) for k in ("groups", "KB", "NCH", "dual"))
-            ctas_per_rank = (g + 1) // 2 if dual else g
-            per_cycle = kb * nch * (g * 4096 + ctas_per_rank * 8192)
+        sh = streamed_shape(desc)
+        if sh:
+            shape, per_cycle = sh
             # one launch of a quarter second or more at full tensor load runs
             # under the power cap, so the sustained figure is the peak
             peaks, src = _peaks()
@@ -228,7 +237,7 @@ def large_workloads(S, W, torch, stream, pool=None):
                                             f"burst 2 x bf16_tflops = {fp8b:.1f}",
                              "operand_bytes_per_cycle": per_cycle,
                              "operand_TBps_into_SMs": per_cycle * C / t / 1e12,
-                             "shape": {k: int(v) for k, v in shape.items()}}
+                             "shape": shape}
         if cfg["kind"] == "gi":
             r["p_s"] = float((E.min(dim=1).values.cpu().numpy() == -off).mean())
         if pool is not None:
