@@ -51,7 +51,8 @@ using namespace tc;
 // flight (~75 B/clk with about 192 KB outstanding, ~23 with one 12 KB stage of
 // one K-block) and with the size of each copy: at N = 2500 (single mode) three
 // stages of 6 K-blocks (72 KB, one 24 KB and one 48 KB copy each) anneal in
-// 0.227 s, four of 4 K-blocks in 0.254 s, six of 3 in 0.286 s.  Dual mode keeps
+// 0.227 s, four of 4 K-blocks in 0.254 s, six of 3 in 0.286 s (two of 9: 0.224 s,
+// within the run-to-run spread, with no stage left to overlap a refill).  Dual mode keeps
 // three stages of 4 K-blocks (64 KB each; two stages of 6 took 0.311 s instead
 // of 0.268 s on SK N = 8192).
 constexpr int kABytes = 128 * 32;   // one K-block of A
